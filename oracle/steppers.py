@@ -1,0 +1,105 @@
+"""Oracle: implicit time steps of the diffusion, hyperdiffusion and Cahn-Hilliard
+workloads, and the FP64 reference for FP32-stored right-hand sides.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+State arrays are interleaved ``(N, M)`` (column m = simulation m).  Every step
+builds its right-hand side from the previous state and solves with the shared
+matrix through :mod:`oracle.banded`.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import banded, matrices
+
+__all__ = [
+    "SharedTri", "SharedPenta",
+    "diffusion_be_step", "diffusion_cn_rhs", "hyper_be_step", "hyper_cn_rhs",
+    "ch_rhs", "ch_step", "solve_fp32_rhs",
+]
+
+
+class SharedTri:
+    """A shared tridiagonal matrix, factorised once (section 3.1, Algorithm 1)."""
+
+    def __init__(self, a, b, c):
+        self.a, self.b, self.c = (np.asarray(v, dtype=np.float64) for v in (a, b, c))
+        self.bh, self.ch = banded.tri_factor(self.a, self.b, self.c)
+
+    def solve(self, d):
+        return banded.tri_solve(self.a, self.bh, self.ch, d)
+
+    def solve_adjoint(self, g):
+        return banded.tri_solve_adjoint(self.a, self.bh, self.ch, g)
+
+    def apply(self, x):
+        return matrices.apply_tri(self.a, self.b, self.c, x)
+
+
+class SharedPenta:
+    """A shared pentadiagonal matrix, factorised once (section 4.1, Algorithm 3)."""
+
+    def __init__(self, a, b, c, d, e):
+        self.diags = tuple(np.asarray(v, dtype=np.float64) for v in (a, b, c, d, e))
+        self.factors = banded.penta_factor(*self.diags)
+
+    def solve(self, f):
+        return banded.penta_solve(*self.factors, f)
+
+    def solve_adjoint(self, g):
+        return banded.penta_solve_adjoint(*self.factors, g)
+
+    def apply(self, x):
+        return matrices.apply_penta(*self.diags, x)
+
+
+def diffusion_be_step(A: SharedTri, C):
+    """Backward Euler: (I + r K) C^{n+1} = C^n."""
+    return A.solve(C)
+
+
+def diffusion_cn_rhs(N, sigma, C):
+    """Crank-Nicolson right-hand side of section 3.2's scheme, with Dirichlet rows:
+    sigma C_{i-1} + (1 - 2 sigma) C_i + sigma C_{i+1} = (I - sigma K) C."""
+    sub, dia, sup = matrices.d2_dirichlet(N)
+    return np.asarray(C, dtype=np.float64) + sigma * matrices.apply_tri(sub, dia, sup, C)
+
+
+def hyper_be_step(A: SharedPenta, C):
+    """Backward Euler for hyperdiffusion: (I + r D4) C^{n+1} = C^n."""
+    return A.solve(C)
+
+
+def hyper_cn_rhs(N, sigma, C, closure="hinged"):
+    """Crank-Nicolson right-hand side of section 4.2's scheme:
+    -sigma C_{i-2} + 4 sigma C_{i-1} + (1 - 6 sigma) C_i + 4 sigma C_{i+1} - sigma C_{i+2}
+    = (I - sigma D4) C, with the same D4 closure as the left-hand side."""
+    if closure == "hinged":
+        D4 = matrices.square_tridiag(*matrices.d2_dirichlet(N))
+    else:
+        D4 = matrices.d4_truncated(N)
+    return np.asarray(C, dtype=np.float64) - sigma * matrices.apply_penta(*D4, C)
+
+
+def ch_rhs(C, alpha):
+    """Right-hand side of the semi-implicit Cahn-Hilliard scheme (section 5.1):
+    f = C^n + alpha * D2_N (C^3 - C)^n, alpha = dt / dx^2 (dx = 1 in grid units),
+    with the no-flux closure of D2_N.  (Section 5.1 prints f_i without the C^n
+    term; the scheme it discretises has C^n on the right-hand side.)"""
+    C = np.asarray(C, dtype=np.float64)
+    N = C.shape[0]
+    nl = C * C * C - C
+    sub, dia, sup = matrices.d2_noflux(N)
+    return C + alpha * matrices.apply_tri(sub, dia, sup, nl)
+
+
+def ch_step(A: SharedPenta, C, alpha):
+    """One semi-implicit Cahn-Hilliard step: (I + sigma D4_N) C^{n+1} = ch_rhs(C^n)."""
+    return A.solve(ch_rhs(C, alpha))
+
+
+def solve_fp32_rhs(A, b32):
+    """FP64 reference for a right-hand side stored in FP32: the FP32 values are
+    promoted exactly to FP64 and solved with the FP64 oracle."""
+    return A.solve(np.asarray(b32, dtype=np.float32).astype(np.float64))
