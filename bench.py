@@ -1,0 +1,350 @@
+"""Benchmark of the shared-LHS batched solve on GB300.
+
+Workload (one "step"): one batched solve of the FP64 pentadiagonal hyperdiffusion
+system A = I + 0.25 D4 (hinged closure), N = 1024 unknowns, 65536 right-hand
+sides drawn i.i.d. N(0, 1), interleaved layout; the shared factors are computed
+once before timing (the paper times only the solve loop, section 3.4).  The
+inputs (2 x 512 MiB) exceed the 126 MiB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) each rank solves its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+
+--impl reference times the plain FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (there is no reference GPU implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shared-LHS batched solves/s & HBM GB/s vs peak; fused/adjoint step/s vs plain"
+UNIT = "batched solves/s"
+WORKLOAD = "penta_hyper: FP64 pentadiagonal A=I+0.25*D4 (hinged), N=1024, M=65536 RHS ~ N(0,1), interleaved"
+N_ROWS = 1024
+M_SYS = 65536
+R_COEF = 0.25
+SEED = 2
+# FP64 flops per element of one pentadiagonal solve: forward 2 FMA + 1 MUL, backward 2 FMA.
+FLOPS_PER_ELT = 9
+BYTES_PER_ELT = 16  # read the RHS once, write the solution once (FP64)
+SM_COUNT = 152
+SM_MAX_GHZ = 2.07
+# FP64 FMA issue rate of GB300: 2 per clock per SM (nominal 1.25 TFLOP/s); peak in TFLOP/s.
+FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * SM_MAX_GHZ / 1e3
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def hbm_peak():
+    p = measured_peaks()
+    if "hbm_gbs" in p:
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks sampler
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(target_seconds=10.0, sample_systems=8192):
+    """The FP64 oracle (NumPy, one core) on a bounded sample of the workload: the
+    first `sample_systems` systems, full N, repeated until ~target_seconds.
+    Returns (batched solves/s scaled to the full M, description)."""
+    import numpy as np
+
+    import synth
+    from oracle import banded, matrices
+
+    diags = matrices.hyperdiffusion_matrix(N_ROWS, R_COEF, "hinged")
+    fac = banded.penta_factor(*diags)
+    rhs = synth.rhs_normal(seed=SEED, N=N_ROWS, M=sample_systems)
+    runs = 0
+    t0 = time.perf_counter()
+    while True:
+        banded.penta_solve(*fac, rhs)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= target_seconds:
+            break
+    value = runs * (sample_systems / M_SYS) / el
+    desc = (f"{runs} oracle solves of {sample_systems} of the {M_SYS} systems (full N={N_ROWS}) "
+            f"in {el:.1f} s; solves/s scaled by {sample_systems}/{M_SYS}")
+    _ = np
+    return value, desc, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    total_runs = 0
+    t_all = 0.0
+    desc = ""
+    for _ in range(args.warmup):
+        cpu_baseline(target_seconds=0.0, sample_systems=1024)
+    for _ in range(args.steps):
+        v, desc, el = cpu_baseline(target_seconds=min(10.0, 60.0 / max(args.steps, 1)),
+                                   sample_systems=4096)
+        total_runs += v * el
+        t_all += el
+    value = total_runs / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_ROWS, "M": M_SYS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU timing
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2107_05395_gb300", "csrc", "sweep.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "penta_sweep_f64_N1024_M65536.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2107_05395_gb300 as sb
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    fac = sb.sb_factor_shared_penta(*sb.sb_build_matrix("hinged", N_ROWS, R_COEF))
+    rhs = synth.torch_normal(SEED + 1000 * rank, N_ROWS, M_SYS, torch.float64, "cuda")
+    x = torch.empty_like(rhs)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sb.sb_solve_batched(fac, rhs, x, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    h_rhs = torch.empty((N_ROWS, M_SYS), dtype=torch.float64, pin_memory=True)
+    h_rhs.copy_(rhs)
+    h_x = torch.empty_like(h_rhs, pin_memory=True)
+    d_rhs = torch.empty_like(rhs)
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        d_rhs.copy_(h_rhs, non_blocking=True)
+        sb.sb_solve_batched(fac, d_rhs, x, stream=stream)
+        h_x.copy_(x, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    avg_launch_s = float(np.mean(launch_ms)) / 1e3
+    elts = N_ROWS * M_SYS
+    flops = FLOPS_PER_ELT * elts
+    achieved_tflops = flops / avg_launch_s / 1e12
+    hbm, hbm_src = hbm_peak()
+    achieved_gbs = BYTES_PER_ELT * elts / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, desc, _ = cpu_baseline()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_ROWS, "M": M_SYS, "closure": "hinged",
+                   "r": R_COEF, "l2": "inputs (2 x 512 MiB) exceed L2; no flush",
+                   "parallelism": f"replicas x{world} (independent batches)"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                     "traffic": traffic,
+                     "kernel": "banded_sweep_kernel<double,P=2> (native FP64)",
+                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm, "peak_source": hbm_src}},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT,
+                "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "launch_ms": {"mean": float(np.mean(launch_ms)), "min": float(np.min(launch_ms)),
+                      "max": float(np.max(launch_ms))},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,148 @@
+/*
+ * sbsolve.h -- C ABI of the shared-LHS batched banded solver for GB300 (sm_103a).
+ *
+ * The problem (the paper's "single A, multiple b" statement, section 1 and
+ * section 2): many tridiagonal or pentadiagonal systems A x_m = b_m, m = 0..M-1,
+ * share ONE left-hand-side matrix A.  A is factorised once on the host in FP64
+ * (Algorithm 1 for tridiagonal, Algorithm 3 / section 4.1 for pentadiagonal) and a
+ * single device copy of its factors is kept; every right-hand side is swept
+ * forward and back (Algorithms 2 and 4) in the interleaved layout of Fig. 2.
+ *
+ * Layout.  A batch of M systems of N unknowns is one array with element (i, m)
+ * at index i*ld + m (system index fastest), 0 <= i < N, 0 <= m < M, ld >= M.
+ * Columns M <= m < ld are never read or written.
+ *
+ * Conventions shared by every call.
+ *   - Return 0 on success, a negative SB_ERR_* code otherwise; no call throws.
+ *     sb_last_error() gives a message for the last failure on this host thread.
+ *   - Device pointers must be device (or managed) memory on the device that was
+ *     current when the factor was created; the library checks this and rejects
+ *     host pointers.  They must be aligned to the element size.
+ *   - Solves are asynchronous on `stream` (a cudaStream_t passed as void*, NULL =
+ *     the legacy default stream).  The status covers argument checks and the
+ *     launch only.
+ *   - `x` may be the same pointer as `rhs` (in-place, as in the paper); any
+ *     other overlap of the two arrays is rejected.
+ *   - A factor handle is immutable once created: it may be used concurrently
+ *     from several streams and host threads.  The caller owns every buffer it
+ *     passes; the library owns only the factor's device copy.
+ */
+#ifndef SBSOLVE_H
+#define SBSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SB_OK                0
+#define SB_ERR_INVALID_ARG  -1  /* bad size, null or misaligned pointer, host pointer, overlap */
+#define SB_ERR_SINGULAR     -2  /* zero or non-finite pivot while factorising (row in message) */
+#define SB_ERR_CUDA         -3  /* a CUDA runtime call or kernel launch failed */
+#define SB_ERR_ALLOC        -4  /* device or host allocation failed */
+#define SB_ERR_UNSUPPORTED  -5  /* valid request this build does not implement */
+
+/* Element type of right-hand sides and solutions in device memory. */
+typedef enum { SB_F64 = 0, SB_F32 = 1 } sb_dtype;
+
+/* Opaque factor of one shared matrix.  Owns a device copy of the factors. */
+typedef struct sb_factor sb_factor;
+
+/*
+ * sb_factor_shared_tri -- factorise a shared tridiagonal matrix (section 3.1,
+ * Algorithm 1: ch_1 = c_1/b_1; bh_i = b_i - a_i ch_{i-1}, ch_i = c_i/bh_i).
+ *
+ *   N        number of unknowns, N >= 1.
+ *   a, b, c  host arrays of N doubles: sub-diagonal (a[0] ignored), diagonal,
+ *            super-diagonal (c[N-1] ignored); row i is a[i] x[i-1] + b[i] x[i]
+ *            + c[i] x[i+1].  Read only during the call.
+ *   out      receives the new handle (set to NULL on failure).
+ *
+ * No pivoting (as in the paper): a zero or non-finite pivot bh_i returns
+ * SB_ERR_SINGULAR and names the row.  The factors are copied to the current
+ * CUDA device; free the handle with sb_factor_destroy.
+ */
+int sb_factor_shared_tri(int64_t N, const double* a, const double* b, const double* c,
+                         sb_factor** out);
+
+/*
+ * sb_factor_shared_penta -- factorise a shared pentadiagonal matrix A = L R
+ * (section 4.1; Algorithm 3 read with the section's equations).
+ *
+ *   a, b, c, d, e  host arrays of N doubles: the diagonals at offsets -2, -1, 0,
+ *                  +1, +2 (row i is a[i] x[i-2] + b[i] x[i-1] + c[i] x[i]
+ *                  + d[i] x[i+1] + e[i] x[i+2]); entries that fall outside the
+ *                  matrix are ignored.
+ * Other arguments and errors as for sb_factor_shared_tri.
+ */
+int sb_factor_shared_penta(int64_t N, const double* a, const double* b, const double* c,
+                           const double* d, const double* e, sb_factor** out);
+
+/* Release a handle and its device memory (NULL is a no-op).  Waits for nothing:
+ * the caller must make sure no solve that uses it is still running. */
+void sb_factor_destroy(sb_factor* f);
+
+/* Bandwidth (1 = tridiagonal, 2 = pentadiagonal) and N of a handle; returns
+ * SB_ERR_INVALID_ARG for a NULL handle or NULL outputs. */
+int sb_factor_info(const sb_factor* f, int* half_bandwidth, int64_t* N);
+
+/*
+ * sb_solve_batched -- solve A x_m = rhs_m for m = 0..M-1 with the shared factors
+ * (forward and backward sweeps of Algorithms 2 and 4), one device pass.
+ *
+ *   rhs, x   device arrays of N*ld elements of `dtype` in the interleaved layout;
+ *            x may equal rhs.
+ *   M        number of systems (M = 0 is a no-op), ld >= M the row stride.
+ *   dtype    SB_F64: FP64 storage and arithmetic.  SB_F32: FP32 storage and
+ *            arithmetic with the FP64 factors rounded to FP32.
+ */
+int sb_solve_batched(const sb_factor* f, const void* rhs, void* x, int64_t M, int64_t ld,
+                     sb_dtype dtype, void* stream);
+
+/*
+ * sb_solve_batched_adjoint -- solve A^T y_m = rhs_m with the same factors
+ * (no counterpart in the paper: A^T = U^T L^T for A = L U, or R^T L^T for
+ * A = L R, swept forward then back).  Arguments as for sb_solve_batched.
+ */
+int sb_solve_batched_adjoint(const sb_factor* f, const void* rhs, void* x, int64_t M,
+                             int64_t ld, sb_dtype dtype, void* stream);
+
+/*
+ * Shared matrices of the finite-difference workloads (S1 of the hot path).
+ * Each is I + coef * K for an operator K:
+ *   SB_MAT_DIFFUSION_DIRICHLET  K = tridiag(-1, 2, -1) with the stencil truncated at
+ *                               the first and last rows (backward-Euler / left-hand
+ *                               side of section 3.2's scheme); tridiagonal.
+ *   SB_MAT_HYPER_HINGED         K = D2 * D2 with D2 = tridiag(1, -2, 1) truncated:
+ *                               interior rows (1, -4, 6, -4, 1) of section 4.2,
+ *                               first/last rows (5, -4, 1), (-4, 6, -4, 1).
+ *   SB_MAT_HYPER_TRUNCATED      K = Toeplitz (1, -4, 6, -4, 1) cut at the edges.
+ *   SB_MAT_CH_NOFLUX            K = D2N * D2N with the cell-centred Neumann
+ *                               D2N = rows (-1, 1), (1, -2, 1), ..., (1, -1): the
+ *                               implicit matrix of section 5.1 with no-flux ends
+ *                               (coef = dt * gamma in grid units).
+ * `diags` is a host array of (2P+1)*N doubles (P = 1 for the diffusion matrix, 2
+ * otherwise), diagonal-major: diags[k*N + i] is row i of the diagonal at offset
+ * k - P; entries outside the matrix are written as 0.  Host only; no GPU needed.
+ * Returns SB_ERR_INVALID_ARG for an unknown kind, N < 1, a NULL or non-finite input.
+ */
+#define SB_MAT_DIFFUSION_DIRICHLET 1
+#define SB_MAT_HYPER_HINGED        2
+#define SB_MAT_HYPER_TRUNCATED     3
+#define SB_MAT_CH_NOFLUX           4
+int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char* sb_last_error(void);
+
+/* Library version string. */
+const char* sb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBSOLVE_H */

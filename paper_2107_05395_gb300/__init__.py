@@ -1,0 +1,20 @@
+"""paper_2107_05395_gb300 -- shared-LHS batched tridiagonal / pentadiagonal solves
+for GB300 (sm_103a).
+
+Many systems A x_m = b_m share one banded matrix A (the setting of "A Batched GPU
+Methodology for Numerical Solutions of Partial Differential Equations", sections
+2-4).  A is factorised once in FP64 on the host; one device copy of its factors
+is staged per CTA and broadcast; every right-hand side, stored interleaved
+(element (i, m) at i*ld + m, Fig. 2), is swept forward and back by hand-written
+CUDA kernels behind the C ABI in ``include/sbsolve.h``.
+
+This package is the Python side of that ABI: ctypes marshalling only.  Build the
+library with ``python -m paper_2107_05395_gb300.build``.
+"""
+from ._lib import (  # noqa: F401
+    SB_ERR_ALLOC, SB_ERR_CUDA, SB_ERR_INVALID_ARG, SB_ERR_SINGULAR, SB_ERR_UNSUPPORTED,
+    SB_F32, SB_F64, SB_OK, SIGNATURES, MATRIX_KINDS, Factor, SbError, lib, sb_build_matrix,
+    sb_factor_info,
+    sb_factor_shared_penta, sb_factor_shared_tri, sb_last_error, sb_solve_batched,
+    sb_solve_batched_adjoint, sb_version,
+)

@@ -1,0 +1,222 @@
+"""ctypes binding of ``libsbsolve.so`` (the C ABI declared in ``include/sbsolve.h``).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Device buffers are passed as torch CUDA tensors (their ``data_ptr``)
+or as raw integer device addresses; host diagonals as NumPy arrays.  The library
+is loaded from this package directory; if it is missing the import fails with
+instructions instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsbsolve.so")
+
+SB_OK = 0
+SB_ERR_INVALID_ARG = -1
+SB_ERR_SINGULAR = -2
+SB_ERR_CUDA = -3
+SB_ERR_ALLOC = -4
+SB_ERR_UNSUPPORTED = -5
+SB_F64 = 0
+SB_F32 = 1
+SB_MAT_DIFFUSION_DIRICHLET = 1
+SB_MAT_HYPER_HINGED = 2
+SB_MAT_HYPER_TRUNCATED = 3
+SB_MAT_CH_NOFLUX = 4
+MATRIX_KINDS = {"diffusion": 1, "hinged": 2, "truncated": 3, "ch_noflux": 4}
+
+_ERR_NAMES = {
+    SB_ERR_INVALID_ARG: "SB_ERR_INVALID_ARG",
+    SB_ERR_SINGULAR: "SB_ERR_SINGULAR",
+    SB_ERR_CUDA: "SB_ERR_CUDA",
+    SB_ERR_ALLOC: "SB_ERR_ALLOC",
+    SB_ERR_UNSUPPORTED: "SB_ERR_UNSUPPORTED",
+}
+
+
+class SbError(RuntimeError):
+    """A negative status returned by the library, with its sb_last_error() text."""
+
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+_lib = None
+
+_c_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); the full exported surface of include/sbsolve.h
+SIGNATURES = {
+    "sb_factor_shared_tri": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
+    "sb_factor_shared_penta": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
+    "sb_factor_destroy": (None, [_vp]),
+    "sb_factor_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_c_i64)]),
+    "sb_solve_batched": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, _vp]),
+    "sb_solve_batched_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, _vp]),
+    "sb_build_matrix": (ctypes.c_int, [ctypes.c_int, _c_i64, ctypes.c_double, _dp]),
+    "sb_last_error": (ctypes.c_char_p, []),
+    "sb_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library (loaded on first use).  Raises if it was never built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2107_05395_gb300.build` "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SB_OK:
+        raise SbError(rc, lib().sb_last_error().decode())
+
+
+def _host_f64(v, N):
+    arr = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    if arr.shape != (N,):
+        raise ValueError(f"diagonal must have shape ({N},), got {arr.shape}")
+    return arr
+
+
+def _dev_ptr(t):
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t, dtype):
+    if dtype is not None:
+        return dtype
+    import torch
+    if t.dtype == torch.float64:
+        return SB_F64
+    if t.dtype == torch.float32:
+        return SB_F32
+    raise TypeError(f"unsupported tensor dtype {t.dtype}")
+
+
+def _batch_shape(t, N, M, ld):
+    """(M, ld) for a tensor of shape (N, ld) unless given explicitly."""
+    if isinstance(t, int):
+        if M is None or ld is None:
+            raise ValueError("M and ld are required with raw device pointers")
+        return M, ld
+    if t.dim() != 2 or t.shape[0] != N or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous (N={N}, ld) tensor, got {tuple(t.shape)}")
+    ld = t.shape[1] if ld is None else ld
+    M = ld if M is None else M
+    return M, ld
+
+
+class Factor:
+    """Owns one sb_factor handle (a single device copy of the shared factors)."""
+
+    def __init__(self, handle: int, P: int, N: int, diags):
+        self.handle = ctypes.c_void_p(handle)
+        self.P = P
+        self.N = N
+        self.diags = tuple(np.array(d, dtype=np.float64) for d in diags)
+
+    @property
+    def kind(self):
+        return "tri" if self.P == 1 else "penta"
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().sb_factor_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sb_factor_shared_tri(a, b, c) -> Factor:
+    """Factorise the shared tridiagonal matrix (sub a, diag b, super c) once."""
+    N = len(b)
+    arrs = [_host_f64(v, N) for v in (a, b, c)]
+    h = ctypes.c_void_p()
+    _check(lib().sb_factor_shared_tri(N, *[x.ctypes.data_as(_dp) for x in arrs], ctypes.byref(h)))
+    return Factor(h.value, 1, N, arrs)
+
+
+def sb_factor_shared_penta(a, b, c, d, e) -> Factor:
+    """Factorise the shared pentadiagonal matrix (offsets -2..+2) once."""
+    N = len(c)
+    arrs = [_host_f64(v, N) for v in (a, b, c, d, e)]
+    h = ctypes.c_void_p()
+    _check(lib().sb_factor_shared_penta(N, *[x.ctypes.data_as(_dp) for x in arrs], ctypes.byref(h)))
+    return Factor(h.value, 2, N, arrs)
+
+
+def sb_factor_info(f: Factor):
+    P = ctypes.c_int()
+    N = ctypes.c_int64()
+    _check(lib().sb_factor_info(f.handle, ctypes.byref(P), ctypes.byref(N)))
+    return P.value, N.value
+
+
+def _solve(fn, f, rhs, x, M, ld, dtype, stream):
+    x = rhs if x is None else x
+    M, ld = _batch_shape(rhs, f.N, M, ld)
+    code = _dtype_code(rhs, dtype) if not isinstance(rhs, int) else dtype
+    _check(fn(f.handle, _dev_ptr(rhs), _dev_ptr(x), M, ld, code, _stream_handle(stream)))
+    return x
+
+
+def sb_solve_batched(f: Factor, rhs, x=None, M=None, ld=None, dtype=None, stream=None):
+    """x_m = A^{-1} rhs_m for all systems (asynchronous on ``stream``).  ``x``
+    defaults to ``rhs`` (in place)."""
+    return _solve(lib().sb_solve_batched, f, rhs, x, M, ld, dtype, stream)
+
+
+def sb_solve_batched_adjoint(f: Factor, rhs, x=None, M=None, ld=None, dtype=None, stream=None):
+    """x_m = A^{-T} rhs_m for all systems, with the same factors."""
+    return _solve(lib().sb_solve_batched_adjoint, f, rhs, x, M, ld, dtype, stream)
+
+
+def sb_build_matrix(kind, N: int, coef: float):
+    """Diagonals of a workload matrix I + coef*K (see include/sbsolve.h) as a
+    tuple of 3 (tridiagonal) or 5 (pentadiagonal) NumPy arrays, offsets -P..P."""
+    code = MATRIX_KINDS[kind] if isinstance(kind, str) else int(kind)
+    P = 1 if code == SB_MAT_DIFFUSION_DIRICHLET else 2
+    out = np.zeros((2 * P + 1) * N, dtype=np.float64)
+    _check(lib().sb_build_matrix(code, N, float(coef), out.ctypes.data_as(_dp)))
+    return tuple(out.reshape(2 * P + 1, N))
+
+
+def sb_last_error() -> str:
+    return lib().sb_last_error().decode()
+
+
+def sb_version() -> str:
+    return lib().sb_version().decode()

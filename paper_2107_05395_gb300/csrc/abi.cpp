@@ -1,0 +1,441 @@
+// Host side of the sbsolve C ABI: errors, argument checks, the FP64 shared-matrix
+// factorisations, and the device copy of their coefficients.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include <cuda.h>
+
+#include "sb_internal.h"
+
+namespace sb {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SB_OK;
+  cudaGetLastError();  // clear the sticky-free error state of the runtime
+  return fail(e == cudaErrorMemoryAllocation ? SB_ERR_ALLOC : SB_ERR_CUDA, "%s failed: %s", what,
+              cudaGetErrorString(e));
+}
+
+DeviceGuard::DeviceGuard(int device) {
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    prev = -1;
+  }
+  if (device >= 0 && device != prev) rc = cuda_check(cudaSetDevice(device), "cudaSetDevice");
+}
+
+DeviceGuard::~DeviceGuard() {
+  int cur = -1;
+  if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+int sm_count(int device) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  if (device < 0 || device >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[device] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cache[device] = v;
+  }
+  return cache[device];
+}
+
+// cuMemGetAddressRange, looked up through the runtime so that the library does
+// not link the driver library directly (it then loads on machines without one).
+typedef CUresult (*RangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+static RangeFn range_fn() {
+  static RangeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<RangeFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int check_device_range(const void* p, size_t bytes, size_t align, int device, const char* name) {
+  if (p == nullptr) return fail(SB_ERR_INVALID_ARG, "%s is NULL", name);
+  if (align > 1 && (reinterpret_cast<uintptr_t>(p) % align) != 0)
+    return fail(SB_ERR_INVALID_ARG, "%s is not aligned to %zu bytes", name, align);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SB_ERR_INVALID_ARG, "%s is not a pointer known to CUDA (%s)", name,
+                cudaGetErrorString(e));
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(SB_ERR_INVALID_ARG, "%s must be device or managed memory (got a host pointer)",
+                name);
+  if (attr.type == cudaMemoryTypeDevice && attr.device != device)
+    return fail(SB_ERR_INVALID_ARG, "%s lives on device %d, the factor on device %d", name,
+                attr.device, device);
+  if (attr.type == cudaMemoryTypeDevice && bytes > 0) {
+    // The whole range [p, p + bytes) must lie inside one allocation.
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    RangeFn fn = range_fn();
+    if (fn == nullptr) return fail(SB_ERR_CUDA, "cuMemGetAddressRange is unavailable");
+    CUresult r = fn(&base, &size, reinterpret_cast<CUdeviceptr>(p));
+    if (r != CUDA_SUCCESS)
+      return fail(SB_ERR_INVALID_ARG, "%s: cannot query its allocation (CUresult %d)", name,
+                  (int)r);
+    uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+    if (lo + bytes > static_cast<uintptr_t>(base) + size)
+      return fail(SB_ERR_INVALID_ARG,
+                  "%s: %zu bytes from the pointer run past the end of its allocation "
+                  "(%zu bytes left)",
+                  name, bytes, (size_t)(static_cast<uintptr_t>(base) + size - lo));
+  }
+  return SB_OK;
+}
+
+int check_alias(const void* a, const void* b, size_t bytes, const char* na, const char* nb) {
+  if (a == b || bytes == 0) return SB_OK;
+  uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  if (x < y + bytes && y < x + bytes)
+    return fail(SB_ERR_INVALID_ARG, "%s and %s overlap without being the same array", na, nb);
+  return SB_OK;
+}
+
+// ------------------------------------------------------ factorisations (FP64)
+
+static bool finite_all(const double* v, int64_t lo, int64_t hi) {
+  for (int64_t i = lo; i < hi; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+// Section 3.1 / Algorithm 1: bh_0 = b_0, ch_0 = c_0/b_0, bh_i = b_i - a_i ch_{i-1},
+// ch_i = c_i / bh_i.  Fills the primal and adjoint coefficient rows (P = 1).
+static int factor_tri_host(int64_t N, const double* a, const double* b, const double* c,
+                           std::vector<double>& coef) {
+  std::vector<double> bh(N), ch(N, 0.0);
+  for (int64_t i = 0; i < N; ++i) {
+    bh[i] = (i == 0) ? b[0] : b[i] - a[i] * ch[i - 1];
+    if (bh[i] == 0.0 || !std::isfinite(bh[i]))
+      return fail(SB_ERR_SINGULAR, "zero or non-finite pivot at row %lld", (long long)i);
+    if (i + 1 < N) ch[i] = c[i] / bh[i];
+  }
+  const int64_t W = 2;  // P + 1
+  coef.assign(2 * op_block_len(1, N), 0.0);
+  double* pf = coef.data();            // primal forward  {a_i, 1/bh_i}
+  double* pb = pf + W * N;             // primal backward {ch_i, 1}
+  double* af = pb + W * N;             // adjoint forward {ch_{i-1}, 1}
+  double* ab = af + W * N;             // adjoint backward {a_{i+1}, 1/bh_i}
+  for (int64_t i = 0; i < N; ++i) {
+    const double ib = 1.0 / bh[i];
+    pf[W * i + 0] = (i > 0) ? a[i] : 0.0;
+    pf[W * i + 1] = ib;
+    pb[W * i + 0] = (i + 1 < N) ? ch[i] : 0.0;
+    pb[W * i + 1] = 1.0;
+    af[W * i + 0] = (i > 0) ? ch[i - 1] : 0.0;
+    af[W * i + 1] = 1.0;
+    ab[W * i + 0] = (i + 1 < N) ? a[i + 1] : 0.0;
+    ab[W * i + 1] = ib;
+  }
+  return SB_OK;
+}
+
+// Section 4.1 (Algorithm 3 read with the section's equations), as one recurrence
+// with out-of-range terms zero:
+//   beta_i  = b_i - a_i gamma_{i-2};  alpha_i = c_i - a_i delta_{i-2} - beta_i gamma_{i-1}
+//   gamma_i = (d_i - beta_i delta_{i-1}) / alpha_i;  delta_i = e_i / alpha_i;  eps_i = a_i
+static int factor_penta_host(int64_t N, const double* a, const double* b, const double* c,
+                             const double* d, const double* e, std::vector<double>& coef) {
+  std::vector<double> al(N), be(N, 0.0), ga(N, 0.0), de(N, 0.0), ep(N, 0.0);
+  auto G = [&](int64_t j) { return j >= 0 ? ga[j] : 0.0; };
+  auto D = [&](int64_t j) { return j >= 0 ? de[j] : 0.0; };
+  for (int64_t i = 0; i < N; ++i) {
+    const double ai = (i >= 2) ? a[i] : 0.0;
+    const double bi = (i >= 1) ? b[i] : 0.0;
+    const double di = (i + 1 < N) ? d[i] : 0.0;
+    const double ei = (i + 2 < N) ? e[i] : 0.0;
+    be[i] = bi - ai * G(i - 2);
+    al[i] = c[i] - ai * D(i - 2) - be[i] * G(i - 1);
+    if (al[i] == 0.0 || !std::isfinite(al[i]))
+      return fail(SB_ERR_SINGULAR, "zero or non-finite pivot at row %lld", (long long)i);
+    ga[i] = (di - be[i] * D(i - 1)) / al[i];
+    de[i] = ei / al[i];
+    ep[i] = ai;
+  }
+  const int64_t W = 3;
+  coef.assign(2 * op_block_len(2, N), 0.0);
+  double* pf = coef.data();  // primal forward  {beta_i, eps_i, 1/alpha_i}
+  double* pb = pf + W * N;   // primal backward {gamma_i, delta_i, 1}
+  double* af = pb + W * N;   // adjoint forward {gamma_{i-1}, delta_{i-2}, 1}
+  double* ab = af + W * N;   // adjoint backward {beta_{i+1}, eps_{i+2}, 1/alpha_i}
+  for (int64_t i = 0; i < N; ++i) {
+    const double ia = 1.0 / al[i];
+    pf[W * i + 0] = be[i];
+    pf[W * i + 1] = ep[i];
+    pf[W * i + 2] = ia;
+    pb[W * i + 0] = ga[i];
+    pb[W * i + 1] = de[i];
+    pb[W * i + 2] = 1.0;
+    af[W * i + 0] = (i >= 1) ? ga[i - 1] : 0.0;
+    af[W * i + 1] = (i >= 2) ? de[i - 2] : 0.0;
+    af[W * i + 2] = 1.0;
+    ab[W * i + 0] = (i + 1 < N) ? be[i + 1] : 0.0;
+    ab[W * i + 1] = (i + 2 < N) ? ep[i + 2] : 0.0;
+    ab[W * i + 2] = ia;
+  }
+  return SB_OK;
+}
+
+static int upload_factor(sb_factor* f) {
+  const size_t nc = f->h_coef.size(), nd = f->h_diag.size();
+  SB_CUDA(cudaMalloc(&f->coef64, nc * sizeof(double)));
+  SB_CUDA(cudaMalloc(&f->coef32, nc * sizeof(float)));
+  SB_CUDA(cudaMalloc(&f->diag64, nd * sizeof(double)));
+  std::vector<float> c32(nc);
+  for (size_t k = 0; k < nc; ++k) c32[k] = static_cast<float>(f->h_coef[k]);
+  SB_CUDA(cudaMemcpy(f->coef64, f->h_coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(f->coef32, c32.data(), nc * sizeof(float), cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(f->diag64, f->h_diag.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
+  return SB_OK;
+}
+
+static void free_factor(sb_factor* f) {
+  if (!f) return;
+  if (f->device >= 0) {
+    DeviceGuard g(f->device);
+    if (f->coef64) cudaFree(f->coef64);
+    if (f->coef32) cudaFree(f->coef32);
+    if (f->diag64) cudaFree(f->diag64);
+  }
+  delete f;
+}
+
+static int make_factor(int P, int64_t N, const double* const* diags, sb_factor** out) {
+  if (out == nullptr) return fail(SB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 1) return fail(SB_ERR_INVALID_ARG, "N must be >= 1 (got %lld)", (long long)N);
+  if (N > (int64_t)1 << 28) return fail(SB_ERR_INVALID_ARG, "N too large (%lld)", (long long)N);
+  const int nd = 2 * P + 1;
+  for (int k = 0; k < nd; ++k) {
+    if (diags[k] == nullptr) return fail(SB_ERR_INVALID_ARG, "diagonal %d is NULL", k);
+    const int off = k - P;  // offset of this diagonal
+    const int64_t lo = off < 0 ? -off : 0, hi = off > 0 ? N - off : N;
+    if (hi > lo && !finite_all(diags[k], lo, hi))
+      return fail(SB_ERR_INVALID_ARG, "diagonal at offset %d has a non-finite entry", off);
+  }
+  sb_factor* f = new (std::nothrow) sb_factor();
+  if (!f) return fail(SB_ERR_ALLOC, "host allocation failed");
+  f->P = P;
+  f->N = N;
+  int rc = (P == 1) ? factor_tri_host(N, diags[0], diags[1], diags[2], f->h_coef)
+                    : factor_penta_host(N, diags[0], diags[1], diags[2], diags[3], diags[4],
+                                        f->h_coef);
+  if (rc != SB_OK) {
+    delete f;
+    return rc;
+  }
+  f->h_diag.assign((size_t)nd * N, 0.0);
+  for (int k = 0; k < nd; ++k) {
+    const int off = k - P;
+    for (int64_t i = 0; i < N; ++i) {
+      const int64_t j = i + off;
+      f->h_diag[(size_t)k * N + i] = (j >= 0 && j < N) ? diags[k][i] : 0.0;
+    }
+  }
+  if (cudaGetDevice(&f->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete f;
+    return fail(SB_ERR_CUDA, "no CUDA device is available");
+  }
+  rc = upload_factor(f);
+  if (rc != SB_OK) {
+    free_factor(f);
+    return rc;
+  }
+  *out = f;
+  return SB_OK;
+}
+
+// Square of a tridiagonal operator T given row-wise by (lo, mid, up):
+// (T T)[i][i+o] = sum over k = i-1..i+1 of T[i][k] T[k][i+o], o = -2..2.
+static void square_tridiagonal(int64_t N, const std::vector<double>& lo,
+                               const std::vector<double>& mid, const std::vector<double>& up,
+                               std::vector<double>& out /* 5*N, diagonal-major */) {
+  auto T = [&](int64_t i, int64_t k) -> double {
+    if (i < 0 || i >= N || k < 0 || k >= N) return 0.0;
+    if (k == i) return mid[i];
+    if (k == i - 1) return lo[i];
+    if (k == i + 1) return up[i];
+    return 0.0;
+  };
+  out.assign(5 * N, 0.0);
+  for (int64_t i = 0; i < N; ++i)
+    for (int o = -2; o <= 2; ++o) {
+      const int64_t j = i + o;
+      if (j < 0 || j >= N) continue;
+      double s = 0.0;
+      for (int64_t k = i - 1; k <= i + 1; ++k) s += T(i, k) * T(k, j);
+      out[(o + 2) * N + i] = s;
+    }
+}
+
+int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, int* P) {
+  if (N < 1) return fail(SB_ERR_INVALID_ARG, "N must be >= 1 (got %lld)", (long long)N);
+  if (!std::isfinite(coef)) return fail(SB_ERR_INVALID_ARG, "coefficient is not finite");
+  std::vector<double> lo(N, 1.0), mid(N, -2.0), up(N, 1.0), K;
+  lo[0] = 0.0;
+  up[N - 1] = 0.0;
+  switch (kind) {
+    case SB_MAT_DIFFUSION_DIRICHLET:
+      *P = 1;
+      diags.assign(3 * N, 0.0);
+      for (int64_t i = 0; i < N; ++i) {
+        diags[i] = (i > 0) ? -coef : 0.0;
+        diags[N + i] = 1.0 + 2.0 * coef;
+        diags[2 * N + i] = (i + 1 < N) ? -coef : 0.0;
+      }
+      return SB_OK;
+    case SB_MAT_HYPER_HINGED:
+      square_tridiagonal(N, lo, mid, up, K);
+      break;
+    case SB_MAT_HYPER_TRUNCATED: {
+      const double st[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+      K.assign(5 * N, 0.0);
+      for (int o = -2; o <= 2; ++o)
+        for (int64_t i = 0; i < N; ++i)
+          if (i + o >= 0 && i + o < N) K[(o + 2) * N + i] = st[o + 2];
+      break;
+    }
+    case SB_MAT_CH_NOFLUX:
+      mid[0] += 1.0;      // ghost cell C_{-1} = C_0
+      mid[N - 1] += 1.0;  // ghost cell C_N = C_{N-1}
+      square_tridiagonal(N, lo, mid, up, K);
+      break;
+    default:
+      return fail(SB_ERR_INVALID_ARG, "unknown matrix kind %d", kind);
+  }
+  *P = 2;
+  diags.assign(5 * N, 0.0);
+  for (int k = 0; k < 5; ++k)
+    for (int64_t i = 0; i < N; ++i)
+      diags[k * N + i] = (k == 2 ? 1.0 : 0.0) + coef * K[k * N + i];
+  for (int k = 0; k < 5; ++k)  // exact zeros outside the matrix
+    for (int64_t i = 0; i < N; ++i)
+      if (i + (k - 2) < 0 || i + (k - 2) >= N) diags[k * N + i] = 0.0;
+  return SB_OK;
+}
+
+static size_t dtype_size(sb_dtype t) { return t == SB_F64 ? 8 : (t == SB_F32 ? 4 : 0); }
+
+// Common checks of a batched solve; on success fills `bytes`.
+static int check_solve_args(const sb_factor* f, const void* rhs, const void* x, int64_t M,
+                            int64_t ld, sb_dtype dtype) {
+  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  const size_t es = dtype_size(dtype);
+  if (es == 0) return fail(SB_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  if (M < 0) return fail(SB_ERR_INVALID_ARG, "M must be >= 0 (got %lld)", (long long)M);
+  if (ld < M || ld < 1)
+    return fail(SB_ERR_INVALID_ARG, "ld must be >= max(M, 1) (got ld=%lld, M=%lld)",
+                (long long)ld, (long long)M);
+  if (ld > ((int64_t)1 << 40) / f->N)
+    return fail(SB_ERR_INVALID_ARG, "N*ld too large");
+  if (M == 0) return SB_OK;
+  const size_t bytes = (size_t)((f->N - 1) * ld + M) * es;
+  SB_TRY(check_device_range(rhs, bytes, es, f->device, "rhs"));
+  SB_TRY(check_device_range(x, bytes, es, f->device, "x"));
+  SB_TRY(check_alias(rhs, x, bytes, "rhs", "x"));
+  return SB_OK;
+}
+
+}  // namespace sb
+
+using namespace sb;
+
+extern "C" {
+
+int sb_factor_shared_tri(int64_t N, const double* a, const double* b, const double* c,
+                         sb_factor** out) {
+  clear_error();
+  const double* d[3] = {a, b, c};
+  return make_factor(1, N, d, out);
+}
+
+int sb_factor_shared_penta(int64_t N, const double* a, const double* b, const double* c,
+                           const double* d, const double* e, sb_factor** out) {
+  clear_error();
+  const double* g[5] = {a, b, c, d, e};
+  return make_factor(2, N, g, out);
+}
+
+void sb_factor_destroy(sb_factor* f) { free_factor(f); }
+
+int sb_factor_info(const sb_factor* f, int* half_bandwidth, int64_t* N) {
+  clear_error();
+  if (!f || !half_bandwidth || !N) return fail(SB_ERR_INVALID_ARG, "NULL argument");
+  *half_bandwidth = f->P;
+  *N = f->N;
+  return SB_OK;
+}
+
+int sb_solve_batched(const sb_factor* f, const void* rhs, void* x, int64_t M, int64_t ld,
+                     sb_dtype dtype, void* stream) {
+  clear_error();
+  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  SB_TRY(check_solve_args(f, rhs, x, M, ld, dtype));
+  if (M == 0) return SB_OK;
+  return launch_banded_sweep(f, OP_PRIMAL, rhs, x, M, ld, dtype, (cudaStream_t)stream);
+}
+
+int sb_solve_batched_adjoint(const sb_factor* f, const void* rhs, void* x, int64_t M,
+                             int64_t ld, sb_dtype dtype, void* stream) {
+  clear_error();
+  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  SB_TRY(check_solve_args(f, rhs, x, M, ld, dtype));
+  if (M == 0) return SB_OK;
+  return launch_banded_sweep(f, OP_ADJOINT, rhs, x, M, ld, dtype, (cudaStream_t)stream);
+}
+
+int sb_build_matrix(int kind, int64_t N, double coef, double* diags) {
+  clear_error();
+  if (diags == nullptr) return fail(SB_ERR_INVALID_ARG, "diags is NULL");
+  std::vector<double> v;
+  int P = 0;
+  SB_TRY(build_matrix(kind, N, coef, v, &P));
+  std::memcpy(diags, v.data(), v.size() * sizeof(double));
+  return SB_OK;
+}
+
+const char* sb_last_error(void) { return g_last_error.c_str(); }
+
+const char* sb_version(void) { return "sbsolve 0.1 (sm_103a)"; }
+
+}  // extern "C"

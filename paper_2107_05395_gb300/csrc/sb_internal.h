@@ -1,0 +1,88 @@
+// Internal declarations of the sbsolve library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sbsolve.h"
+
+namespace sb {
+
+// ---------------------------------------------------------------- errors
+// Records a message for sb_last_error() and returns `code`.
+int fail(int code, const char* fmt, ...);
+// Clears the message (called at the start of every ABI entry point).
+void clear_error();
+// Turns a CUDA error into SB_ERR_CUDA with the call site; returns SB_OK on success.
+int cuda_check(cudaError_t e, const char* what);
+
+#define SB_CUDA(call)                                              \
+  do {                                                             \
+    int rc_ = ::sb::cuda_check((call), #call);                     \
+    if (rc_ != SB_OK) return rc_;                                  \
+  } while (0)
+
+#define SB_TRY(expr)                                               \
+  do {                                                             \
+    int rc_ = (expr);                                              \
+    if (rc_ != SB_OK) return rc_;                                  \
+  } while (0)
+
+// ----------------------------------------------------- coefficient blocks
+// Both solves (A and A^T) run the same two recurrences over the interleaved
+// array, with P = half bandwidth (1 tridiagonal, 2 pentadiagonal):
+//   forward : u_i = (r_i - sum_{k=1..P} p_{i,k} u_{i-k}) * s_i
+//   backward: x_i = (u_i - sum_{k=1..P} q_{i,k} x_{i+k}) * t_i
+// For A (primal) s_i is the reciprocal pivot and t_i = 1; for A^T (adjoint)
+// s_i = 1 and t_i is the reciprocal pivot.  Each row stores (P + 1) values:
+// the P coupling coefficients then the scale.  Coefficients that reach outside
+// the matrix are exactly 0, so the sweeps need no edge cases.
+// One "op" block = [forward rows 0..N-1][backward rows 0..N-1].
+inline int64_t op_block_len(int P, int64_t N) { return 2 * (P + 1) * N; }
+
+enum Op { OP_PRIMAL = 0, OP_ADJOINT = 1 };
+
+}  // namespace sb
+
+struct sb_factor {
+  int P = 0;                 // half bandwidth
+  int64_t N = 0;
+  int device = -1;
+  double* coef64 = nullptr;  // device: [primal block | adjoint block], FP64
+  float* coef32 = nullptr;   // device: same values rounded to FP32
+  double* diag64 = nullptr;  // device: the original 2P+1 diagonals, diagonal-major (d * N + i)
+  std::vector<double> h_coef;  // host copy of coef64
+  std::vector<double> h_diag;  // host copy of diag64
+};
+
+namespace sb {
+
+// ------------------------------------------------------------ validation
+// Checks that [p, p + bytes) is device/managed memory of `device`, aligned to
+// `align`.  Host pointers and out-of-allocation ranges are rejected.
+int check_device_range(const void* p, size_t bytes, size_t align, int device, const char* name);
+// Rejects partial overlap of two ranges (identical start pointers are allowed).
+int check_alias(const void* a, const void* b, size_t bytes, const char* na, const char* nb);
+
+// RAII guard that makes `device` current and restores the previous device.
+struct DeviceGuard {
+  int prev = -1;
+  int rc = SB_OK;
+  explicit DeviceGuard(int device);
+  ~DeviceGuard();
+};
+
+int sm_count(int device);
+
+// Diagonals of a workload matrix (sb_build_matrix); sets *P to 1 or 2.
+int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, int* P);
+
+// Launchers implemented in sweep.cu.
+int launch_banded_sweep(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M,
+                        int64_t ld, sb_dtype dtype, cudaStream_t stream);
+
+}  // namespace sb

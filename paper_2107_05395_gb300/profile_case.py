@@ -1,0 +1,49 @@
+"""Runs a few launches of one solver kernel on a chosen size, for profilers.
+
+    python -m paper_2107_05395_gb300.profile_case --kind penta --N 1024 --M 32768 --launches 3
+
+Everything goes through the C ABI; inputs are seeded N(0, 1) drawn on the device.
+The default case keeps the inputs above the L2 size (so DRAM counters mean
+something) while holding well under a GB on the device.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", choices=["tri", "penta"], default="penta")
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--M", type=int, default=32768)
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--launches", type=int, default=3)
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_2107_05395_gb300 as sb
+    import synth
+
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    if args.kind == "tri":
+        fac = sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", args.N, 0.5))
+    else:
+        fac = sb.sb_factor_shared_penta(*sb.sb_build_matrix("hinged", args.N, 0.25))
+    rhs = synth.torch_normal(2, args.N, args.M, dt, "cuda")
+    x = torch.empty_like(rhs)
+    fn = sb.sb_solve_batched_adjoint if args.adjoint else sb.sb_solve_batched
+    for _ in range(args.launches):
+        fn(fac, rhs, x)
+    torch.cuda.synchronize()
+    print(f"ok: {args.launches} launches of {args.kind} N={args.N} M={args.M} {args.dtype}"
+          f"{' adjoint' if args.adjoint else ''}")
+
+
+if __name__ == "__main__":
+    main()

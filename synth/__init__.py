@@ -121,17 +121,22 @@ def random_penta_diagonals(seed: int, N: int, margin: float = 0.5, stream: int =
 def sine_mode_block(N: int, modes) -> np.ndarray:
     """Columns are the discrete Dirichlet sine modes sin((i+1) k pi / (N+1)),
     i = 0..N-1, one column per k in ``modes``.  Shape ``(N, len(modes))``."""
-    i = np.arange(N, dtype=np.float64)[:, None] + 1.0
-    k = np.asarray(modes, dtype=np.float64)[None, :]
-    return np.sin(i * k * np.pi / (N + 1))
+    # the integer phase (i+1)k is reduced modulo 2(N+1) exactly before scaling, so
+    # the argument stays in [0, 2 pi) and each sample is accurate to about an ulp
+    i = np.arange(1, N + 1, dtype=np.int64)[:, None]
+    k = np.asarray(modes, dtype=np.int64)[None, :]
+    phase = (i * k) % (2 * (N + 1))
+    return np.sin(phase.astype(np.float64) * np.pi / (N + 1))
 
 
 def cosine_mode_block(N: int, modes, amplitude: float = 1.0) -> np.ndarray:
     """Columns are amplitude * cos(k pi (i + 1/2) / N), the cell-centred Neumann
     modes, one per k in ``modes``.  Shape ``(N, len(modes))``."""
-    i = np.arange(N, dtype=np.float64)[:, None] + 0.5
-    k = np.asarray(modes, dtype=np.float64)[None, :]
-    return amplitude * np.cos(k * np.pi * i / N)
+    # cos(k pi (2i+1) / (2N)): the integer phase k(2i+1) is reduced modulo 4N first
+    i = np.arange(N, dtype=np.int64)[:, None]
+    k = np.asarray(modes, dtype=np.int64)[None, :]
+    phase = (k * (2 * i + 1)) % (4 * N)
+    return amplitude * np.cos(phase.astype(np.float64) * np.pi / (2 * N))
 
 
 # --- device-side generators for the full-size workloads (torch Philox stream) ---
