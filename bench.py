@@ -183,9 +183,26 @@ def run_reference(args):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2107_05395_gb300", "csrc", "sweep.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("sweep.cu", "arith.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_05395_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def time_launches(step, stream, steps, warmup):
+    """Per-launch CUDA-event durations (ms) of `step` on `stream`, after warm-up."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
 
 
 def profiled_traffic():
@@ -224,8 +241,14 @@ def run_ours(args):
     x = torch.empty_like(rhs)
     stream = torch.cuda.current_stream()
 
+    arith = args.arith
+    # pick the launch shape of each arithmetic mode with the library's autotuner
+    shapes = {}
+    for mode in ("native", "df32"):
+        shapes[mode] = sb.sb_autotune(fac, rhs, x, arith=mode)
+
     def step():
-        sb.sb_solve_batched(fac, rhs, x, stream=stream)
+        sb.sb_solve_batched_ex(fac, rhs, x, arith=arith, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -270,8 +293,13 @@ def run_ours(args):
 
     def e2e_step():
         d_rhs.copy_(h_rhs, non_blocking=True)
-        sb.sb_solve_batched(fac, d_rhs, x, stream=stream)
+        sb.sb_solve_batched_ex(fac, d_rhs, x, arith=arith, stream=stream)
         h_x.copy_(x, non_blocking=True)
+
+    # the other arithmetic mode on the same workload, timed the same way
+    other = "native" if arith == "df32" else "df32"
+    other_ms = time_launches(lambda: sb.sb_solve_batched_ex(fac, rhs, x, arith=other, stream=stream),
+                             stream, max(5, min(args.steps, 20)), 3)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -304,24 +332,43 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         v, desc, _ = cpu_baseline()
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    other_s = float(np.mean(other_ms)) / 1e3
+    if arith == "df32":
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "traffic": traffic,
+                "kernel": "sweep_kernel<DFArith,P=2> (double-float arithmetic, FP64 I/O)",
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "alu_fp64_equiv": {"achieved": achieved_tflops, "unit": "TFLOP/s"}}
+        dtype = "f64 (double-float arithmetic)"
+    else:
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                "traffic": traffic,
+                "kernel": "sweep_kernel<NativeArith<double>,P=2> (native FP64)",
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm, "peak_source": hbm_src}}
+        dtype = "f64"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_ROWS, "M": M_SYS, "closure": "hinged",
-                   "r": R_COEF, "l2": "inputs (2 x 512 MiB) exceed L2; no flush",
+                   "r": R_COEF, "arith": arith, "l2": "inputs (2 x 512 MiB) exceed L2; no flush",
+                   "shape": {"threads_ctas_per_sm_spt": list(shapes[arith][0]),
+                             "autotune_ms": shapes[arith][1]},
                    "parallelism": f"replicas x{world} (independent batches)"},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                     "traffic": traffic,
-                     "kernel": "banded_sweep_kernel<double,P=2> (native FP64)",
-                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm, "peak_source": hbm_src}},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8},
+        "extras": {
+            f"solve_{other}": {"shape": list(shapes[other][0]),
+                               "ms_per_solve": float(np.mean(other_ms)),
+                               "batched_solves_per_s": 1.0 / other_s,
+                               "hbm_gbs": BYTES_PER_ELT * elts / other_s / 1e9},
+        },
         "gpu_launches": args.steps,
         "clocks": clocks,
         "launch_ms": {"mean": float(np.mean(launch_ms)), "min": float(np.min(launch_ms)),
@@ -340,6 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arith", choices=["native", "df32"], default="native")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -48,6 +48,21 @@ extern "C" {
 /* Element type of right-hand sides and solutions in device memory. */
 typedef enum { SB_F64 = 0, SB_F32 = 1 } sb_dtype;
 
+/*
+ * Arithmetic of a sweep.
+ *   SB_ARITH_NATIVE  the storage type's own arithmetic (FP64 for SB_F64, FP32 for
+ *                    SB_F32; FP32 when an FP32 right-hand side is solved into an
+ *                    FP64 solution).
+ *   SB_ARITH_DF32    double-float: each value is the unevaluated sum of two FP32
+ *                    numbers (about 48 significant bits, relative rounding about
+ *                    2^-47 per operation), computed on the FP32 pipe.  Inputs are
+ *                    FP64 (or FP32) and the solution is FP64.  On GB300 the FP64 pipe
+ *                    issues 2 operations per clock per SM against 128 for FP32, so
+ *                    this mode reaches FP64-level accuracy (1e-13 relative on
+ *                    well-conditioned systems) at several times the speed.
+ */
+typedef enum { SB_ARITH_NATIVE = 0, SB_ARITH_DF32 = 1 } sb_arith;
+
 /* Opaque factor of one shared matrix.  Owns a device copy of the factors. */
 typedef struct sb_factor sb_factor;
 
@@ -109,6 +124,55 @@ int sb_solve_batched(const sb_factor* f, const void* rhs, void* x, int64_t M, in
  */
 int sb_solve_batched_adjoint(const sb_factor* f, const void* rhs, void* x, int64_t M,
                              int64_t ld, sb_dtype dtype, void* stream);
+
+/*
+ * sb_solve_batched_ex -- the general form of sb_solve_batched / _adjoint.
+ *
+ *   transpose  0 solves A x = rhs, 1 solves A^T x = rhs.
+ *   rhs_dtype, x_dtype  storage of rhs and x.  Supported combinations:
+ *                SB_ARITH_NATIVE: (F64, F64), (F32, F32), (F32, F64);
+ *                SB_ARITH_DF32:   (F64, F64), (F32, F64).
+ *              Others return SB_ERR_UNSUPPORTED.  x may equal rhs only when the
+ *              two dtypes are the same.
+ * Other arguments as for sb_solve_batched.
+ */
+int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs_dtype,
+                        void* x, sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith,
+                        void* stream);
+
+/*
+ * Launch shape of the sweep kernels: threads per CTA (a multiple of 32 in
+ * [32, 512]), resident CTAs per SM (0 = as many as fit) and systems per thread
+ * (1 or 2: each thread interleaves that many independent recurrences).
+ */
+typedef struct {
+  int threads;
+  int ctas_per_sm;
+  int systems_per_thread;
+} sb_shape;
+
+/* The shape solves with this factor's (half bandwidth, N), arithmetic and dtypes
+ * will use: a stored entry if there is one, else the built-in default. */
+int sb_shape_get(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtype x_dtype,
+                 sb_shape* out);
+
+/* Store a shape for that key (process-wide, on the factor's device); for example
+ * one loaded from a tuning cache.  SB_ERR_INVALID_ARG for an out-of-range shape. */
+int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtype x_dtype,
+                 const sb_shape* shape);
+
+/*
+ * sb_autotune -- time every candidate shape (threads 64..512, CTAs/SM 0..2,
+ * systems per thread 1..2) on the caller's buffers with CUDA events (one warm-up
+ * and the best of three launches each), store the fastest as for sb_shape_set and
+ * return it in *best (and its time in *best_ms; either may be NULL).  x is
+ * overwritten and must differ from rhs; arguments otherwise as for
+ * sb_solve_batched_ex.  Blocking: it synchronises on `stream`.  The autotuner is
+ * this library's own (the paper's kernels have a fixed one-thread-per-system shape).
+ */
+int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs_dtype, void* x,
+                sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, void* stream,
+                sb_shape* best, float* best_ms);
 
 /*
  * Shared matrices of the finite-difference workloads (S1 of the hot path).

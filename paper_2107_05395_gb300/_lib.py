@@ -24,6 +24,9 @@ SB_ERR_ALLOC = -4
 SB_ERR_UNSUPPORTED = -5
 SB_F64 = 0
 SB_F32 = 1
+SB_ARITH_NATIVE = 0
+SB_ARITH_DF32 = 1
+ARITH = {"native": SB_ARITH_NATIVE, "df32": SB_ARITH_DF32}
 SB_MAT_DIFFUSION_DIRICHLET = 1
 SB_MAT_HYPER_HINGED = 2
 SB_MAT_HYPER_TRUNCATED = 3
@@ -61,6 +64,12 @@ SIGNATURES = {
     "sb_factor_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_c_i64)]),
     "sb_solve_batched": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, _vp]),
     "sb_solve_batched_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, _vp]),
+    "sb_solve_batched_ex": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                           _c_i64, _c_i64, ctypes.c_int, _vp]),
+    "sb_shape_get": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "sb_shape_set": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "sb_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _c_i64,
+                                   _c_i64, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_float)]),
     "sb_build_matrix": (ctypes.c_int, [ctypes.c_int, _c_i64, ctypes.c_double, _dp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
@@ -202,6 +211,55 @@ def sb_solve_batched(f: Factor, rhs, x=None, M=None, ld=None, dtype=None, stream
 def sb_solve_batched_adjoint(f: Factor, rhs, x=None, M=None, ld=None, dtype=None, stream=None):
     """x_m = A^{-T} rhs_m for all systems, with the same factors."""
     return _solve(lib().sb_solve_batched_adjoint, f, rhs, x, M, ld, dtype, stream)
+
+
+def sb_solve_batched_ex(f: Factor, rhs, x, transpose=False, arith="native", M=None, ld=None,
+                        rhs_dtype=None, x_dtype=None, stream=None):
+    """General solve: A x = rhs (or A^T x = rhs) with separate rhs / x storage types and
+    an arithmetic mode ("native" or "df32", see include/sbsolve.h)."""
+    M, ld = _batch_shape(rhs, f.N, M, ld)
+    rt = _dtype_code(rhs, rhs_dtype) if not isinstance(rhs, int) else rhs_dtype
+    xt = _dtype_code(x, x_dtype) if not isinstance(x, int) else x_dtype
+    a = ARITH[arith] if isinstance(arith, str) else int(arith)
+    _check(lib().sb_solve_batched_ex(f.handle, 1 if transpose else 0, _dev_ptr(rhs), rt, _dev_ptr(x),
+                                     xt, M, ld, a, _stream_handle(stream)))
+    return x
+
+
+class Shape(ctypes.Structure):
+    """sb_shape: threads per CTA, resident CTAs per SM (0 = max), systems per thread."""
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("systems_per_thread", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.threads, self.ctas_per_sm, self.systems_per_thread)
+
+
+def _arith_code(arith):
+    return ARITH[arith] if isinstance(arith, str) else int(arith)
+
+
+def sb_shape_get(f: Factor, arith="native", rhs_dtype=SB_F64, x_dtype=SB_F64):
+    out = Shape()
+    _check(lib().sb_shape_get(f.handle, _arith_code(arith), rhs_dtype, x_dtype, ctypes.byref(out)))
+    return out.as_tuple()
+
+
+def sb_shape_set(f: Factor, shape, arith="native", rhs_dtype=SB_F64, x_dtype=SB_F64):
+    s = Shape(*shape)
+    _check(lib().sb_shape_set(f.handle, _arith_code(arith), rhs_dtype, x_dtype, ctypes.byref(s)))
+
+
+def sb_autotune(f: Factor, rhs, x, transpose=False, arith="native", M=None, ld=None, stream=None):
+    """Times every candidate launch shape on (rhs, x) and stores the fastest; returns
+    ((threads, ctas_per_sm, systems_per_thread), ms).  Overwrites x; blocking."""
+    M, ld = _batch_shape(rhs, f.N, M, ld)
+    best = Shape()
+    ms = ctypes.c_float()
+    _check(lib().sb_autotune(f.handle, 1 if transpose else 0, _dev_ptr(rhs), _dtype_code(rhs, None),
+                             _dev_ptr(x), _dtype_code(x, None), M, ld, _arith_code(arith),
+                             _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
+    return best.as_tuple(), ms.value
 
 
 def sb_build_matrix(kind, N: int, coef: float):

@@ -1,5 +1,6 @@
 // Host side of the sbsolve C ABI: errors, argument checks, the FP64 shared-matrix
 // factorisations, and the device copy of their coefficients.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -118,10 +119,11 @@ int check_device_range(const void* p, size_t bytes, size_t align, int device, co
   return SB_OK;
 }
 
-int check_alias(const void* a, const void* b, size_t bytes, const char* na, const char* nb) {
-  if (a == b || bytes == 0) return SB_OK;
+int check_alias(const void* a, size_t abytes, const void* b, size_t bbytes, const char* na,
+                const char* nb) {
+  if (a == b || abytes == 0 || bbytes == 0) return SB_OK;
   uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-  if (x < y + bytes && y < x + bytes)
+  if (x < y + bbytes && y < x + abytes)
     return fail(SB_ERR_INVALID_ARG, "%s and %s overlap without being the same array", na, nb);
   return SB_OK;
 }
@@ -145,22 +147,21 @@ static int factor_tri_host(int64_t N, const double* a, const double* b, const do
       return fail(SB_ERR_SINGULAR, "zero or non-finite pivot at row %lld", (long long)i);
     if (i + 1 < N) ch[i] = c[i] / bh[i];
   }
-  const int64_t W = 2;  // P + 1
+  const int64_t W = 2;  // P + 1; rows prescaled by the reciprocal pivot
   coef.assign(2 * op_block_len(1, N), 0.0);
-  double* pf = coef.data();            // primal forward  {a_i, 1/bh_i}
-  double* pb = pf + W * N;             // primal backward {ch_i, 1}
-  double* af = pb + W * N;             // adjoint forward {ch_{i-1}, 1}
-  double* ab = af + W * N;             // adjoint backward {a_{i+1}, 1/bh_i}
+  double* pf = coef.data();  // primal forward  {1/bh_i, a_i/bh_i}
+  double* pb = pf + W * N;   // primal backward {1, ch_i}
+  double* af = pb + W * N;   // adjoint forward {1, ch_{i-1}}
+  double* ab = af + W * N;   // adjoint backward {1/bh_i, a_{i+1}/bh_i}
   for (int64_t i = 0; i < N; ++i) {
-    const double ib = 1.0 / bh[i];
-    pf[W * i + 0] = (i > 0) ? a[i] : 0.0;
-    pf[W * i + 1] = ib;
-    pb[W * i + 0] = (i + 1 < N) ? ch[i] : 0.0;
-    pb[W * i + 1] = 1.0;
-    af[W * i + 0] = (i > 0) ? ch[i - 1] : 0.0;
-    af[W * i + 1] = 1.0;
-    ab[W * i + 0] = (i + 1 < N) ? a[i + 1] : 0.0;
-    ab[W * i + 1] = ib;
+    pf[W * i + 0] = 1.0 / bh[i];
+    pf[W * i + 1] = (i > 0) ? a[i] / bh[i] : 0.0;
+    pb[W * i + 0] = 1.0;
+    pb[W * i + 1] = (i + 1 < N) ? ch[i] : 0.0;
+    af[W * i + 0] = 1.0;
+    af[W * i + 1] = (i > 0) ? ch[i - 1] : 0.0;
+    ab[W * i + 0] = 1.0 / bh[i];
+    ab[W * i + 1] = (i + 1 < N) ? a[i + 1] / bh[i] : 0.0;
   }
   return SB_OK;
 }
@@ -187,26 +188,25 @@ static int factor_penta_host(int64_t N, const double* a, const double* b, const 
     de[i] = ei / al[i];
     ep[i] = ai;
   }
-  const int64_t W = 3;
+  const int64_t W = 3;  // rows prescaled by the reciprocal pivot
   coef.assign(2 * op_block_len(2, N), 0.0);
-  double* pf = coef.data();  // primal forward  {beta_i, eps_i, 1/alpha_i}
-  double* pb = pf + W * N;   // primal backward {gamma_i, delta_i, 1}
-  double* af = pb + W * N;   // adjoint forward {gamma_{i-1}, delta_{i-2}, 1}
-  double* ab = af + W * N;   // adjoint backward {beta_{i+1}, eps_{i+2}, 1/alpha_i}
+  double* pf = coef.data();  // primal forward  {1/alpha_i, beta_i/alpha_i, eps_i/alpha_i}
+  double* pb = pf + W * N;   // primal backward {1, gamma_i, delta_i}
+  double* af = pb + W * N;   // adjoint forward {1, gamma_{i-1}, delta_{i-2}}
+  double* ab = af + W * N;   // adjoint backward {1/alpha_i, beta_{i+1}/alpha_i, eps_{i+2}/alpha_i}
   for (int64_t i = 0; i < N; ++i) {
-    const double ia = 1.0 / al[i];
-    pf[W * i + 0] = be[i];
-    pf[W * i + 1] = ep[i];
-    pf[W * i + 2] = ia;
-    pb[W * i + 0] = ga[i];
-    pb[W * i + 1] = de[i];
-    pb[W * i + 2] = 1.0;
-    af[W * i + 0] = (i >= 1) ? ga[i - 1] : 0.0;
-    af[W * i + 1] = (i >= 2) ? de[i - 2] : 0.0;
-    af[W * i + 2] = 1.0;
-    ab[W * i + 0] = (i + 1 < N) ? be[i + 1] : 0.0;
-    ab[W * i + 1] = (i + 2 < N) ? ep[i + 2] : 0.0;
-    ab[W * i + 2] = ia;
+    pf[W * i + 0] = 1.0 / al[i];
+    pf[W * i + 1] = be[i] / al[i];
+    pf[W * i + 2] = ep[i] / al[i];
+    pb[W * i + 0] = 1.0;
+    pb[W * i + 1] = ga[i];
+    pb[W * i + 2] = de[i];
+    af[W * i + 0] = 1.0;
+    af[W * i + 1] = (i >= 1) ? ga[i - 1] : 0.0;
+    af[W * i + 2] = (i >= 2) ? de[i - 2] : 0.0;
+    ab[W * i + 0] = 1.0 / al[i];
+    ab[W * i + 1] = (i + 1 < N) ? be[i + 1] / al[i] : 0.0;
+    ab[W * i + 2] = (i + 2 < N) ? ep[i + 2] / al[i] : 0.0;
   }
   return SB_OK;
 }
@@ -215,9 +215,16 @@ static int upload_factor(sb_factor* f) {
   const size_t nc = f->h_coef.size(), nd = f->h_diag.size();
   SB_CUDA(cudaMalloc(&f->coef64, nc * sizeof(double)));
   SB_CUDA(cudaMalloc(&f->coef32, nc * sizeof(float)));
+  SB_CUDA(cudaMalloc(&f->coefdf, 2 * nc * sizeof(float)));
   SB_CUDA(cudaMalloc(&f->diag64, nd * sizeof(double)));
-  std::vector<float> c32(nc);
-  for (size_t k = 0; k < nc; ++k) c32[k] = static_cast<float>(f->h_coef[k]);
+  std::vector<float> c32(nc), cdf(2 * nc);
+  for (size_t k = 0; k < nc; ++k) {
+    const double v = f->h_coef[k];
+    c32[k] = static_cast<float>(v);
+    cdf[2 * k] = static_cast<float>(v);  // hi: v rounded to FP32
+    cdf[2 * k + 1] = static_cast<float>(v - static_cast<double>(cdf[2 * k]));  // lo
+  }
+  SB_CUDA(cudaMemcpy(f->coefdf, cdf.data(), 2 * nc * sizeof(float), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->coef64, f->h_coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->coef32, c32.data(), nc * sizeof(float), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->diag64, f->h_diag.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
@@ -230,6 +237,7 @@ static void free_factor(sb_factor* f) {
     DeviceGuard g(f->device);
     if (f->coef64) cudaFree(f->coef64);
     if (f->coef32) cudaFree(f->coef32);
+    if (f->coefdf) cudaFree(f->coefdf);
     if (f->diag64) cudaFree(f->diag64);
   }
   delete f;
@@ -352,24 +360,39 @@ int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, i
 
 static size_t dtype_size(sb_dtype t) { return t == SB_F64 ? 8 : (t == SB_F32 ? 4 : 0); }
 
-// Common checks of a batched solve; on success fills `bytes`.
-static int check_solve_args(const sb_factor* f, const void* rhs, const void* x, int64_t M,
-                            int64_t ld, sb_dtype dtype) {
+// Common checks of a batched solve.
+static int check_solve_args(const sb_factor* f, const void* rhs, sb_dtype rt, const void* x,
+                            sb_dtype xt, int64_t M, int64_t ld) {
   if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
-  const size_t es = dtype_size(dtype);
-  if (es == 0) return fail(SB_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  const size_t rs = dtype_size(rt), xs = dtype_size(xt);
+  if (rs == 0) return fail(SB_ERR_INVALID_ARG, "unknown rhs dtype %d", (int)rt);
+  if (xs == 0) return fail(SB_ERR_INVALID_ARG, "unknown x dtype %d", (int)xt);
   if (M < 0) return fail(SB_ERR_INVALID_ARG, "M must be >= 0 (got %lld)", (long long)M);
   if (ld < M || ld < 1)
     return fail(SB_ERR_INVALID_ARG, "ld must be >= max(M, 1) (got ld=%lld, M=%lld)",
                 (long long)ld, (long long)M);
-  if (ld > ((int64_t)1 << 40) / f->N)
-    return fail(SB_ERR_INVALID_ARG, "N*ld too large");
+  if (ld > ((int64_t)1 << 40) / f->N) return fail(SB_ERR_INVALID_ARG, "N*ld too large");
   if (M == 0) return SB_OK;
-  const size_t bytes = (size_t)((f->N - 1) * ld + M) * es;
-  SB_TRY(check_device_range(rhs, bytes, es, f->device, "rhs"));
-  SB_TRY(check_device_range(x, bytes, es, f->device, "x"));
-  SB_TRY(check_alias(rhs, x, bytes, "rhs", "x"));
+  const size_t elems = (size_t)((f->N - 1) * ld + M);
+  SB_TRY(check_device_range(rhs, elems * rs, rs, f->device, "rhs"));
+  SB_TRY(check_device_range(x, elems * xs, xs, f->device, "x"));
+  if (rhs == x && rt != xt)
+    return fail(SB_ERR_INVALID_ARG, "x may alias rhs only when both have the same dtype");
+  SB_TRY(check_alias(rhs, elems * rs, x, elems * xs, "rhs", "x"));
   return SB_OK;
+}
+
+static int solve_common(const sb_factor* f, Op op, const void* rhs, sb_dtype rt, void* x,
+                        sb_dtype xt, int64_t M, int64_t ld, sb_arith arith, void* stream) {
+  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode %d", (int)arith);
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  SB_TRY(check_solve_args(f, rhs, rt, x, xt, M, ld));
+  if (M == 0) return SB_OK;
+  return launch_sweep(f, op, rhs, rt, x, xt, M, ld, arith, shape_for(f, arith, rt, xt),
+                      (cudaStream_t)stream);
 }
 
 }  // namespace sb
@@ -405,23 +428,23 @@ int sb_factor_info(const sb_factor* f, int* half_bandwidth, int64_t* N) {
 int sb_solve_batched(const sb_factor* f, const void* rhs, void* x, int64_t M, int64_t ld,
                      sb_dtype dtype, void* stream) {
   clear_error();
-  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
-  DeviceGuard g(f->device);
-  SB_TRY(g.rc);
-  SB_TRY(check_solve_args(f, rhs, x, M, ld, dtype));
-  if (M == 0) return SB_OK;
-  return launch_banded_sweep(f, OP_PRIMAL, rhs, x, M, ld, dtype, (cudaStream_t)stream);
+  return solve_common(f, OP_PRIMAL, rhs, dtype, x, dtype, M, ld, SB_ARITH_NATIVE, stream);
 }
 
 int sb_solve_batched_adjoint(const sb_factor* f, const void* rhs, void* x, int64_t M,
                              int64_t ld, sb_dtype dtype, void* stream) {
   clear_error();
-  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
-  DeviceGuard g(f->device);
-  SB_TRY(g.rc);
-  SB_TRY(check_solve_args(f, rhs, x, M, ld, dtype));
-  if (M == 0) return SB_OK;
-  return launch_banded_sweep(f, OP_ADJOINT, rhs, x, M, ld, dtype, (cudaStream_t)stream);
+  return solve_common(f, OP_ADJOINT, rhs, dtype, x, dtype, M, ld, SB_ARITH_NATIVE, stream);
+}
+
+int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs_dtype,
+                        void* x, sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith,
+                        void* stream) {
+  clear_error();
+  if (transpose != 0 && transpose != 1)
+    return fail(SB_ERR_INVALID_ARG, "transpose must be 0 or 1");
+  return solve_common(f, transpose ? OP_ADJOINT : OP_PRIMAL, rhs, rhs_dtype, x, x_dtype, M, ld,
+                      arith, stream);
 }
 
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags) {

@@ -1,0 +1,258 @@
+// Arithmetic policies for the batched sweeps.
+//
+// Every sweep step has the same shape (coefficients prescaled on the host):
+//     out = C0 * in - C1 * v1 - C2 * v2          (C2 only for pentadiagonal)
+// NativeArith<T> evaluates it in T (FP64 or FP32) with fused multiply-adds.
+// DFArith evaluates it in double-float ("df") arithmetic: every value is an
+// unevaluated sum h + l of two FP32 numbers with |l| <= ulp(h), giving about 48
+// significant bits with the FP32 pipe (GB300 issues 64x more FP32 than FP64
+// operations per clock).  The building blocks are the classical error-free
+// transformations: TwoSum (Knuth), Fast2Sum (Dekker) and TwoProd with an FMA.
+// FP64 <-> df conversions of the inputs and outputs use integer operations only
+// (the FP64 conversion instructions run on the slow FP64 pipe); values outside
+// the exponent window of the integer path take an exact FP64 fallback.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#if defined(__CUDACC__)
+#define SB_HD __host__ __device__ __forceinline__
+#else
+#define SB_HD inline
+#endif
+
+namespace sb {
+
+// ------------------------------------------------- portable primitives
+// On the device these are the round-to-nearest intrinsics (never contracted into
+// FMAs); the host versions exist so the same code can be unit-tested on a CPU
+// (compile host code with -ffp-contract=off).
+SB_HD float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+SB_HD float f_sub(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+SB_HD float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+SB_HD float f_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+SB_HD uint32_t f2u(float v) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(v);
+#else
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  return u;
+#endif
+}
+SB_HD float u2f(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float v;
+  std::memcpy(&v, &u, 4);
+  return v;
+#endif
+}
+SB_HD uint32_t d_hi(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint32_t)__double2hiint(v);
+#else
+  uint64_t u;
+  std::memcpy(&u, &v, 8);
+  return (uint32_t)(u >> 32);
+#endif
+}
+SB_HD uint32_t d_lo(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint32_t)__double2loint(v);
+#else
+  uint64_t u;
+  std::memcpy(&u, &v, 8);
+  return (uint32_t)u;
+#endif
+}
+SB_HD double hilo2d(uint32_t hi, uint32_t lo) {
+#ifdef __CUDA_ARCH__
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  const uint64_t u = ((uint64_t)hi << 32) | lo;
+  double v;
+  std::memcpy(&v, &u, 8);
+  return v;
+#endif
+}
+// upper 32 bits of (hi:lo) << s, 0 <= s < 32
+SB_HD uint32_t funnel_l(uint32_t lo, uint32_t hi, uint32_t s) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_l(lo, hi, s);
+#else
+  return (uint32_t)(((((uint64_t)hi << 32) | lo) << s) >> 32);
+#endif
+}
+// (hi:lo) + (bhi:blo) modulo 2^64
+SB_HD void add64(uint32_t lo, uint32_t hi, uint32_t blo, uint32_t bhi, uint32_t* rlo,
+                 uint32_t* rhi) {
+#ifdef __CUDA_ARCH__
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
+      : "=r"(*rlo), "=r"(*rhi)
+      : "r"(lo), "r"(blo), "r"(hi), "r"(bhi));
+#else
+  const uint64_t r = (((uint64_t)hi << 32) | lo) + (((uint64_t)bhi << 32) | blo);
+  *rlo = (uint32_t)r;
+  *rhi = (uint32_t)(r >> 32);
+#endif
+}
+
+// ------------------------------------------------------------- native T
+
+template <typename T>
+struct NativeArith {
+  using V = T;  // working value
+  using C = T;  // coefficient
+  using S = T;  // stored intermediate
+  static SB_HD V zero() { return T(0); }
+  // out = c0*in - c1*v1 (- c2*v2); C0ONE skips the c0 product.
+  template <int P, bool C0ONE>
+  static SB_HD V step(const C* c, V in, V v1, V v2) {
+    V u = C0ONE ? in : in * c[0];
+    u = std::fma(-c[1], v1, u);
+    if constexpr (P == 2) u = std::fma(-c[2], v2, u);
+    return u;
+  }
+  static SB_HD S to_store(V v) { return v; }
+  static SB_HD V from_store(S s) { return s; }
+};
+
+// ---------------------------------------------------------- double-float
+
+struct alignas(8) df {
+  float h, l;
+};
+
+// Knuth's TwoSum: s + e == a + b exactly.
+SB_HD df two_sum(float a, float b) {
+  const float s = f_add(a, b);
+  const float bb = f_sub(s, a);
+  const float e = f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb));
+  return {s, e};
+}
+
+// Dekker's Fast2Sum, valid when |a| >= |b| (or a == 0).
+SB_HD df fast_two_sum(float a, float b) {
+  const float s = f_add(a, b);
+  const float e = f_sub(b, f_sub(s, a));
+  return {s, e};
+}
+
+// Product of a df coefficient and a df value as an unnormalised pair (p, e):
+// p = fl(ch*vh) and e = its exact rounding error + ch*vl + cl*vh (the cl*vl
+// term is below 2^-48 relative and dropped).
+SB_HD df df_mul(df c, df v) {
+  const float p = f_mul(c.h, v.h);
+  float e = f_fma(c.h, v.h, -p);
+  e = f_fma(c.h, v.l, e);
+  e = f_fma(c.l, v.h, e);
+  return {p, e};
+}
+
+// FP64 -> df.  Integer path for 2^-60 <= |v| < 2^100: the high part keeps the
+// sign, exponent and top 23 fraction bits (truncated), the low part the next 23
+// bits, made exact by the subtraction of a power of two (Sterbenz).  The 6
+// lowest fraction bits are dropped (relative error < 2^-47).
+// Exact slow paths of the conversions, kept out of line: if they were inlined the
+// compiler may if-convert them and issue their FP64 instructions (on GB300's slow
+// FP64 pipe) for every element, not only for the rare values that need them.
+#if defined(__CUDACC__)
+__host__ __device__ __noinline__
+#else
+inline
+#endif
+df double_to_df_slow(double v) {
+  const float h = (float)v;  // round to nearest, then the rest
+  return {h, (float)(v - (double)h)};
+}
+
+#if defined(__CUDACC__)
+#define SB_LIKELY(c) __builtin_expect(!!(c), 1)
+#else
+#define SB_LIKELY(c) (c)
+#endif
+
+SB_HD df double_to_df(double v) {
+  const uint32_t hi = d_hi(v), lo = d_lo(v);
+  const uint32_t E = (hi >> 20) & 0x7FFu;
+  if (SB_LIKELY(E - 963u < 160u)) {  // E in [963, 1122]: exponent in [-60, 99]
+    const uint32_t t = funnel_l(lo, hi, 3);                // E[8:0] | top 23 bits
+    const uint32_t hb = (t - (896u << 23)) | (hi & 0x80000000u);
+    const uint32_t bb = (hb & 0xFF800000u) - (23u << 23);  // 2^(e-23) with the sign
+    const uint32_t fb = bb | ((lo >> 6) & 0x7FFFFFu);
+    return {u2f(hb), f_sub(u2f(fb), u2f(bb))};
+  }
+  return double_to_df_slow(v);  // exact fallback (rare)
+}
+
+// FP32 -> FP64 widening with integer operations only (exact): sign, exponent
+// re-biased by 1023 - 127 = 896, fraction shifted into the upper bits.  Zero and
+// FP32 subnormals give (signed) zero; infinities and NaNs are not expected here.
+SB_HD double widen_f32(float v) {
+  const uint32_t b = f2u(v);
+  const uint32_t mag = b & 0x7FFFFFFFu;
+  const uint32_t hi = (mag >= 0x00800000u) ? ((mag >> 3) + (896u << 20)) : 0u;
+  const uint32_t lo = (mag >= 0x00800000u) ? (b << 29) : 0u;
+  return hilo2d(hi | (b & 0x80000000u), lo);
+}
+
+// df -> FP64: h + l rounded to the nearest double.  Both parts are widened exactly
+// with integer operations and added with a single FP64 addition (one FP64-pipe
+// instruction per value instead of two conversions and an addition).
+SB_HD double df_to_double(df x) { return widen_f32(x.h) + widen_f32(x.l); }
+
+struct DFArith {
+  using V = df;
+  using C = df;  // (hi, lo) of a coefficient
+  using S = df;  // stored intermediate (8 bytes, same as FP64)
+  static SB_HD V zero() { return {0.f, 0.f}; }
+  template <int P, bool C0ONE>
+  static SB_HD V step(const C* c, V in, V v1, V v2) {
+    df t0 = C0ONE ? in : df_mul(c[0], in);
+    const df t1 = df_mul(c[1], v1);
+    const df s1 = two_sum(t0.h, -t1.h);
+    float lo = f_sub(t0.l, t1.l);
+    float hi = s1.h;
+    lo = f_add(lo, s1.l);
+    if constexpr (P == 2) {
+      const df t2 = df_mul(c[2], v2);
+      const df s2 = two_sum(hi, -t2.h);
+      lo = f_sub(lo, t2.l);
+      lo = f_add(lo, s2.l);
+      hi = s2.h;
+    }
+    return fast_two_sum(hi, lo);
+  }
+  static SB_HD S to_store(V v) { return v; }
+  static SB_HD V from_store(S s) { return s; }
+};
+
+}  // namespace sb

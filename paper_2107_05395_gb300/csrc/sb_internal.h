@@ -34,17 +34,25 @@ int cuda_check(cudaError_t e, const char* what);
 
 // ----------------------------------------------------- coefficient blocks
 // Both solves (A and A^T) run the same two recurrences over the interleaved
-// array, with P = half bandwidth (1 tridiagonal, 2 pentadiagonal):
-//   forward : u_i = (r_i - sum_{k=1..P} p_{i,k} u_{i-k}) * s_i
-//   backward: x_i = (u_i - sum_{k=1..P} q_{i,k} x_{i+k}) * t_i
-// For A (primal) s_i is the reciprocal pivot and t_i = 1; for A^T (adjoint)
-// s_i = 1 and t_i is the reciprocal pivot.  Each row stores (P + 1) values:
-// the P coupling coefficients then the scale.  Coefficients that reach outside
-// the matrix are exactly 0, so the sweeps need no edge cases.
+// array, with P = half bandwidth (1 tridiagonal, 2 pentadiagonal) and the
+// coefficients prescaled by the reciprocal pivot on the host:
+//   forward : u_i = F0_i r_i - F1_i u_{i-1} - F2_i u_{i-2}
+//   backward: x_i = B0_i u_i - B1_i x_{i+1} - B2_i x_{i+2}
+// For A (primal) F0 is the reciprocal pivot and B0 = 1; for A^T (adjoint)
+// F0 = 1 and B0 is the reciprocal pivot.  Each row stores (P + 1) values
+// (F0, F1[, F2]).  Coefficients that reach outside the matrix are exactly 0, so
+// the sweeps need no edge cases.
 // One "op" block = [forward rows 0..N-1][backward rows 0..N-1].
 inline int64_t op_block_len(int P, int64_t N) { return 2 * (P + 1) * N; }
 
 enum Op { OP_PRIMAL = 0, OP_ADJOINT = 1 };
+
+// Launch shape of the sweep kernel (chosen by default_shape or the autotuner).
+struct SweepShape {
+  int threads = 256;     // threads per CTA (multiple of 32)
+  int ctas_per_sm = 0;   // cap on resident CTAs per SM (0 = occupancy limit)
+  int spt = 1;           // systems per thread (1 or 2)
+};
 
 }  // namespace sb
 
@@ -54,6 +62,7 @@ struct sb_factor {
   int device = -1;
   double* coef64 = nullptr;  // device: [primal block | adjoint block], FP64
   float* coef32 = nullptr;   // device: same values rounded to FP32
+  float* coefdf = nullptr;   // device: same values as (hi, lo) FP32 pairs
   double* diag64 = nullptr;  // device: the original 2P+1 diagonals, diagonal-major (d * N + i)
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64
@@ -65,8 +74,9 @@ namespace sb {
 // Checks that [p, p + bytes) is device/managed memory of `device`, aligned to
 // `align`.  Host pointers and out-of-allocation ranges are rejected.
 int check_device_range(const void* p, size_t bytes, size_t align, int device, const char* name);
-// Rejects partial overlap of two ranges (identical start pointers are allowed).
-int check_alias(const void* a, const void* b, size_t bytes, const char* na, const char* nb);
+// Rejects overlap of [a, a+abytes) and [b, b+bbytes) unless a == b.
+int check_alias(const void* a, size_t abytes, const void* b, size_t bbytes, const char* na,
+                const char* nb);
 
 // RAII guard that makes `device` current and restores the previous device.
 struct DeviceGuard {
@@ -82,7 +92,11 @@ int sm_count(int device);
 int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, int* P);
 
 // Launchers implemented in sweep.cu.
-int launch_banded_sweep(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M,
-                        int64_t ld, sb_dtype dtype, cudaStream_t stream);
+SweepShape default_shape(const sb_factor* f, sb_arith arith);
+// Tuned shape for (device, P, N, arith, dtypes) or the default (tune.cpp).
+SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype xt);
+int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
+                 sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
+                 cudaStream_t stream);
 
 }  // namespace sb

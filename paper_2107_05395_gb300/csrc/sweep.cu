@@ -1,113 +1,186 @@
-// Batched forward/backward sweeps with one shared factor (Algorithms 2 and 4),
-// native arithmetic in the storage type (FP64 or FP32).
+// Batched forward/backward sweeps with one shared factor (Algorithms 2 and 4, and
+// the transposed solve), for every arithmetic policy of arith.cuh.
 //
-// One thread owns one system m; a warp therefore touches 32 consecutive
-// systems, and every row access i*ld + m is one coalesced 256 B (FP64) or 128 B
-// (FP32) transaction per warp.  The shared coefficients (one copy on the device,
-// section 2) are staged once per CTA into shared memory and read as broadcasts.
-// The forward result u is written into x and read back by the backward sweep
-// (in place, as in Algorithm 2); the same thread reads what it wrote, so no
-// synchronisation is needed.  Rows are fetched R at a time into registers so
-// that R independent loads are in flight per thread.
+// Mapping.  One thread owns one system m; a warp owns 32 consecutive systems (a
+// "tile"), so every row access i*ld + m is one coalesced transaction per warp.
+// CTAs are persistent: each stages the shared coefficients into shared memory
+// once (the single device copy of section 2, broadcast from shared memory instead
+// of the caches) and its warps then take tiles round-robin over the grid.
+//
+// Per system: the forward sweep reads the right-hand side and writes its
+// intermediate (A::S, at most the size of an output element) in place into x; the
+// backward sweep reads it back (the same thread, so no synchronisation) and
+// writes the solution over it.  Rows are fetched R at a time into registers with
+// double buffering: the next batch is in flight while the current one is swept.
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
+#include "arith.cuh"
 #include "sb_internal.h"
 
 namespace sb {
 namespace {
 
-constexpr int kThreads = 128;  // threads per CTA (4 warps)
-constexpr int kRows = 8;       // rows fetched ahead per batch
+constexpr int kRows = 8;  // rows per prefetch batch
+
+// ------------------------------------------------------------ conversions
+
+template <class A, typename T>
+struct Conv;
+
+template <typename T>
+struct Conv<NativeArith<T>, T> {
+  static __device__ __forceinline__ T in(T v) { return v; }
+  static __device__ __forceinline__ T out(T v) { return v; }
+};
+template <>
+struct Conv<NativeArith<float>, double> {  // FP32 arithmetic, FP64 output
+  static __device__ __forceinline__ double out(float v) { return (double)v; }
+};
+template <>
+struct Conv<DFArith, double> {
+  static __device__ __forceinline__ df in(double v) { return double_to_df(v); }
+  static __device__ __forceinline__ double out(df v) { return df_to_double(v); }
+};
+template <>
+struct Conv<DFArith, float> {
+  static __device__ __forceinline__ df in(float v) { return {v, 0.f}; }
+};
 
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
 
-// coef: [forward rows][backward rows], (P + 1) values per row (see sb_internal.h).
-template <typename T, int P, bool SCALE_FWD, bool SCALE_BWD, bool SMEM>
-__global__ void __launch_bounds__(kThreads)
-banded_sweep_kernel(const T* __restrict__ coef, int N, int64_t M, int64_t ld,
-                    const T* rhs, T* x, int64_t tiles) {
+// ------------------------------------------------------------------ kernel
+
+// coef: [forward rows][backward rows], (P + 1) coefficients per row:
+//   forward  u_i = F0 r_i - F1 u_{i-1} - F2 u_{i-2}      (F0 == 1 when F_ONE)
+//   backward x_i = B0 u_i - B1 x_{i+1} - B2 x_{i+2}      (B0 == 1 when B_ONE)
+// SPT systems per thread (m and m + 32, ... within a tile of 32*SPT systems) give
+// each thread SPT independent recurrences to interleave; R rows per prefetch batch.
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
+__global__ void __launch_bounds__(512)
+sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld,
+             const TI* rhs, TO* x, int64_t ntiles) {
+  using V = typename A::V;
+  using C = typename A::C;
+  using S = typename A::S;
+  static_assert(sizeof(S) <= sizeof(TO), "intermediate must fit in an output element");
   constexpr int W = P + 1;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* cf;
-  if constexpr (SMEM) {
-    T* s = reinterpret_cast<T*>(smem_raw);
+  C* cs = reinterpret_cast<C*>(smem_raw);
+  {
     const int n = 2 * W * N;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) s[k] = coef[k];
-    __syncthreads();
-    cf = s;
-  } else {
-    cf = coef;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
   }
-  const T* fw = cf;
-  const T* bw = cf + (int64_t)W * N;
+  __syncthreads();
+  const C* fw = cs;
+  const C* bw = cs + W * N;
 
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t m = tile * kThreads + threadIdx.x;
-    if (m >= M) continue;
-    const T* r = rhs + m;
-    T* y = x + m;
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
+       tile += (int64_t)gridDim.x * nw) {
+    const int64_t m0 = tile * (32 * SPT) + lane;
+    if (m0 >= M) continue;
+    bool ok[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) ok[s] = (m0 + 32 * s) < M;
+    const TI* r = rhs + m0;
+    TO* y = x + m0;
+    auto slot = [&](int i, int s) {
+      return reinterpret_cast<S*>(y + (int64_t)i * ld + 32 * s);
+    };
 
-    // forward: u_i = (r_i - p1 u_{i-1} - p2 u_{i-2}) * s_i
-    T u1 = T(0), u2 = T(0);
-    for (int i0 = 0; i0 < N; i0 += kRows) {
-      T v[kRows];
+    // ---- forward sweep
+    V u1[SPT], u2[SPT];
 #pragma unroll
-      for (int j = 0; j < kRows; ++j)
-        if (i0 + j < N) v[j] = ld_stream(r + (int64_t)(i0 + j) * ld);
+    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = A::zero();
+    TI va[R][SPT], vb[R][SPT];
+    auto load_in = [&](TI (&buf)[R][SPT], int i0) {
 #pragma unroll
-      for (int j = 0; j < kRows; ++j) {
+      for (int j = 0; j < R; ++j)
+#pragma unroll
+        for (int s = 0; s < SPT; ++s)
+          if (i0 + j < N && ok[s]) buf[j][s] = ld_stream(r + (int64_t)(i0 + j) * ld + 32 * s);
+    };
+    auto fwd = [&](TI (&buf)[R][SPT], int i0) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
         const int i = i0 + j;
         if (i < N) {
-          const T* c = fw + W * i;
-          T u = v[j] - c[0] * u1;
-          if constexpr (P == 2) u -= c[1] * u2;
-          if constexpr (SCALE_FWD) u *= c[P];
-          y[(int64_t)i * ld] = u;
-          if constexpr (P == 2) u2 = u1;
-          u1 = u;
+          const C* c = fw + W * i;
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            const V u = A::template step<P, F_ONE>(c, Conv<A, TI>::in(buf[j][s]), u1[s], u2[s]);
+            if (ok[s]) *slot(i, s) = A::to_store(u);
+            u2[s] = u1[s];
+            u1[s] = u;
+          }
         }
       }
+    };
+    load_in(va, 0);
+    for (int i0 = 0; i0 < N; i0 += 2 * R) {
+      load_in(vb, i0 + R);
+      fwd(va, i0);
+      load_in(va, i0 + 2 * R);
+      fwd(vb, i0 + R);
     }
-    // backward: x_i = (u_i - q1 x_{i+1} - q2 x_{i+2}) * t_i
-    T x1 = T(0), x2 = T(0);
-    for (int i0 = N - 1; i0 >= 0; i0 -= kRows) {
-      T v[kRows];
+
+    // ---- backward sweep
+    V x1[SPT], x2[SPT];
 #pragma unroll
-      for (int j = 0; j < kRows; ++j)
-        if (i0 - j >= 0) v[j] = y[(int64_t)(i0 - j) * ld];
+    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = A::zero();
+    S sa[R][SPT], sb_[R][SPT];
+    auto load_mid = [&](S (&buf)[R][SPT], int i0) {
 #pragma unroll
-      for (int j = 0; j < kRows; ++j) {
+      for (int j = 0; j < R; ++j)
+#pragma unroll
+        for (int s = 0; s < SPT; ++s)
+          if (i0 - j >= 0 && ok[s]) buf[j][s] = *slot(i0 - j, s);
+    };
+    auto bwd = [&](S (&buf)[R][SPT], int i0) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
         const int i = i0 - j;
         if (i >= 0) {
-          const T* c = bw + W * i;
-          T xi = v[j] - c[0] * x1;
-          if constexpr (P == 2) xi -= c[1] * x2;
-          if constexpr (SCALE_BWD) xi *= c[P];
-          st_stream(y + (int64_t)i * ld, xi);
-          if constexpr (P == 2) x2 = x1;
-          x1 = xi;
+          const C* c = bw + W * i;
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            const V xi = A::template step<P, B_ONE>(c, A::from_store(buf[j][s]), x1[s], x2[s]);
+            if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(xi));
+            x2[s] = x1[s];
+            x1[s] = xi;
+          }
         }
       }
+    };
+    load_mid(sa, N - 1);
+    for (int i0 = N - 1; i0 >= 0; i0 -= 2 * R) {
+      load_mid(sb_, i0 - R);
+      bwd(sa, i0);
+      load_mid(sa, i0 - 2 * R);
+      bwd(sb_, i0 - R);
     }
   }
 }
 
-struct LaunchInfo {
+// ----------------------------------------------------------------- launching
+
+struct Occ {
   int blocks_per_sm = 0;
 };
-
 std::mutex g_occ_mu;
-std::unordered_map<uint64_t, LaunchInfo> g_occ;
+std::unordered_map<uint64_t, Occ> g_occ;
 
 template <typename K>
-int prepare_kernel(K kernel, int device, size_t smem, int* blocks_per_sm) {
-  const uint64_t key = (reinterpret_cast<uint64_t>(reinterpret_cast<const void*>(kernel)) << 8) ^
-                       ((uint64_t)smem << 1) ^ (uint64_t)device * 0x9E3779B97F4A7C15ull;
+int prepare(K kernel, int device, int threads, size_t smem, int* blocks_per_sm) {
+  const uint64_t key = (reinterpret_cast<uint64_t>(reinterpret_cast<const void*>(kernel)) * 31u) ^
+                       ((uint64_t)smem << 20) ^ ((uint64_t)threads << 8) ^ (uint64_t)device;
   {
     std::lock_guard<std::mutex> lk(g_occ_mu);
     auto it = g_occ.find(key);
@@ -116,63 +189,97 @@ int prepare_kernel(K kernel, int device, size_t smem, int* blocks_per_sm) {
       return SB_OK;
     }
   }
-  if (smem > 48 * 1024)
-    SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nb = 0;
-  SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem));
-  if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "kernel cannot be resident with %zu B smem", smem);
+  SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
+  if (nb < 1)
+    return fail(SB_ERR_UNSUPPORTED, "sweep kernel cannot be resident (%d threads, %zu B smem)",
+                threads, smem);
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ[key].blocks_per_sm = nb;
   *blocks_per_sm = nb;
   return SB_OK;
 }
 
-template <typename T, int P, bool SF, bool SB_>
-int launch_typed(const sb_factor* f, const T* coef, const T* rhs, T* x, int64_t M, int64_t ld,
-                 cudaStream_t stream) {
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
+int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
+           int64_t ld, const SweepShape& shape, cudaStream_t stream) {
   const int N = (int)f->N;
-  const size_t coef_bytes = (size_t)2 * (P + 1) * N * sizeof(T);
-  const int64_t tiles = (M + kThreads - 1) / kThreads;
-  const int sms = sm_count(f->device);
+  const size_t smem = (size_t)2 * (P + 1) * N * sizeof(typename A::C);
+  if (smem > 227 * 1024)
+    return fail(SB_ERR_UNSUPPORTED,
+                "N=%d: the shared factors (%zu B) exceed the shared memory of one CTA", N, smem);
+  auto k = sweep_kernel<A, P, F_ONE, B_ONE, TI, TO, SPT, R>;
+  const int threads = shape.threads;
+  if (threads < 32 || threads > 512 || threads % 32 != 0)
+    return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, 512]");
   int nb = 0;
-  // Shared-memory staging when the coefficients fit beside a useful occupancy.
-  if (coef_bytes <= 200 * 1024) {
-    auto k = banded_sweep_kernel<T, P, SF, SB_, true>;
-    SB_TRY(prepare_kernel(k, f->device, coef_bytes, &nb));
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)nb * sms);
-    k<<<(unsigned)grid, kThreads, coef_bytes, stream>>>(coef, N, M, ld, rhs, x, tiles);
-  } else {
-    auto k = banded_sweep_kernel<T, P, SF, SB_, false>;
-    SB_TRY(prepare_kernel(k, f->device, 0, &nb));
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)nb * sms);
-    k<<<(unsigned)grid, kThreads, 0, stream>>>(coef, N, M, ld, rhs, x, tiles);
-  }
-  return cuda_check(cudaGetLastError(), "banded sweep launch");
+  SB_TRY(prepare(k, f->device, threads, smem, &nb));
+  if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
+  const int64_t ntiles = (M + 32 * SPT - 1) / (32 * SPT);
+  const int64_t want = (ntiles + threads / 32 - 1) / (threads / 32);
+  const int64_t grid =
+      std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(f->device)));
+  k<<<(unsigned)grid, threads, smem, stream>>>(coef, N, M, ld, static_cast<const TI*>(rhs),
+                                              static_cast<TO*>(x), ntiles);
+  return cuda_check(cudaGetLastError(), "sweep kernel launch");
+}
+
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO>
+int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
+               int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+  if (shape.spt == 2)
+    return launch<A, P, F_ONE, B_ONE, TI, TO, 2, 4>(f, coef, rhs, x, M, ld, shape, stream);
+  if (shape.spt != 1) return fail(SB_ERR_INVALID_ARG, "systems per thread must be 1 or 2");
+  return launch<A, P, F_ONE, B_ONE, TI, TO, 1, kRows>(f, coef, rhs, x, M, ld, shape, stream);
+}
+
+template <class A, typename TI, typename TO>
+int dispatch_pb(const sb_factor* f, Op op, const typename A::C* base, const void* rhs, void* x,
+                int64_t M, int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+  const typename A::C* c = base + (op == OP_PRIMAL ? 0 : op_block_len(f->P, f->N));
+  if (f->P == 1)
+    return op == OP_PRIMAL
+               ? launch_spt<A, 1, false, true, TI, TO>(f, c, rhs, x, M, ld, shape, stream)
+               : launch_spt<A, 1, true, false, TI, TO>(f, c, rhs, x, M, ld, shape, stream);
+  return op == OP_PRIMAL
+             ? launch_spt<A, 2, false, true, TI, TO>(f, c, rhs, x, M, ld, shape, stream)
+             : launch_spt<A, 2, true, false, TI, TO>(f, c, rhs, x, M, ld, shape, stream);
 }
 
 }  // namespace
 
-int launch_banded_sweep(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M,
-                        int64_t ld, sb_dtype dtype, cudaStream_t stream) {
-  const int64_t blk = op_block_len(f->P, f->N);
-  if (dtype == SB_F64) {
-    const double* c = f->coef64 + (op == OP_PRIMAL ? 0 : blk);
-    const double* r = static_cast<const double*>(rhs);
-    double* y = static_cast<double*>(x);
-    if (f->P == 1)
-      return op == OP_PRIMAL ? launch_typed<double, 1, true, false>(f, c, r, y, M, ld, stream)
-                             : launch_typed<double, 1, false, true>(f, c, r, y, M, ld, stream);
-    return op == OP_PRIMAL ? launch_typed<double, 2, true, false>(f, c, r, y, M, ld, stream)
-                           : launch_typed<double, 2, false, true>(f, c, r, y, M, ld, stream);
+SweepShape default_shape(const sb_factor* f, sb_arith arith) {
+  SweepShape s;
+  s.threads = (arith == SB_ARITH_DF32) ? 128 : 256;
+  s.ctas_per_sm = 0;  // occupancy limit
+  s.spt = 1;
+  (void)f;
+  return s;
+}
+
+int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
+                 sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
+                 cudaStream_t stream) {
+  if (arith == SB_ARITH_NATIVE) {
+    if (rhs_dtype == SB_F64 && x_dtype == SB_F64)
+      return dispatch_pb<NativeArith<double>, double, double>(f, op, f->coef64, rhs, x, M, ld,
+                                                              shape, stream);
+    if (rhs_dtype == SB_F32 && x_dtype == SB_F32)
+      return dispatch_pb<NativeArith<float>, float, float>(f, op, f->coef32, rhs, x, M, ld, shape,
+                                                           stream);
+    if (rhs_dtype == SB_F32 && x_dtype == SB_F64)
+      return dispatch_pb<NativeArith<float>, float, double>(f, op, f->coef32, rhs, x, M, ld,
+                                                            shape, stream);
+  } else if (arith == SB_ARITH_DF32) {
+    const df* c = reinterpret_cast<const df*>(f->coefdf);
+    if (rhs_dtype == SB_F64 && x_dtype == SB_F64)
+      return dispatch_pb<DFArith, double, double>(f, op, c, rhs, x, M, ld, shape, stream);
+    if (rhs_dtype == SB_F32 && x_dtype == SB_F64)
+      return dispatch_pb<DFArith, float, double>(f, op, c, rhs, x, M, ld, shape, stream);
   }
-  const float* c = f->coef32 + (op == OP_PRIMAL ? 0 : blk);
-  const float* r = static_cast<const float*>(rhs);
-  float* y = static_cast<float*>(x);
-  if (f->P == 1)
-    return op == OP_PRIMAL ? launch_typed<float, 1, true, false>(f, c, r, y, M, ld, stream)
-                           : launch_typed<float, 1, false, true>(f, c, r, y, M, ld, stream);
-  return op == OP_PRIMAL ? launch_typed<float, 2, true, false>(f, c, r, y, M, ld, stream)
-                         : launch_typed<float, 2, false, true>(f, c, r, y, M, ld, stream);
+  return fail(SB_ERR_UNSUPPORTED, "unsupported combination: rhs dtype %d, x dtype %d, arith %d",
+              (int)rhs_dtype, (int)x_dtype, (int)arith);
 }
 
 }  // namespace sb

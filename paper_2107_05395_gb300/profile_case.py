@@ -22,7 +22,10 @@ def main():
     ap.add_argument("--M", type=int, default=32768)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--arith", choices=["native", "df32"], default="native")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--autotune", action="store_true", help="pick the launch shape first")
+    ap.add_argument("--shape", default=None, help="threads,ctas_per_sm,systems_per_thread")
     args = ap.parse_args()
 
     import torch
@@ -37,12 +40,18 @@ def main():
         fac = sb.sb_factor_shared_penta(*sb.sb_build_matrix("hinged", args.N, 0.25))
     rhs = synth.torch_normal(2, args.N, args.M, dt, "cuda")
     x = torch.empty_like(rhs)
-    fn = sb.sb_solve_batched_adjoint if args.adjoint else sb.sb_solve_batched
+    if args.shape:
+        sb.sb_shape_set(fac, tuple(int(v) for v in args.shape.split(",")), arith=args.arith,
+                        rhs_dtype=sb.SB_F64 if args.dtype == "f64" else sb.SB_F32,
+                        x_dtype=sb.SB_F64 if args.dtype == "f64" else sb.SB_F32)
+    if args.autotune:
+        shape, ms = sb.sb_autotune(fac, rhs, x, transpose=args.adjoint, arith=args.arith)
+        print(f"autotuned shape {shape} ({ms:.3f} ms)")
     for _ in range(args.launches):
-        fn(fac, rhs, x)
+        sb.sb_solve_batched_ex(fac, rhs, x, transpose=args.adjoint, arith=args.arith)
     torch.cuda.synchronize()
     print(f"ok: {args.launches} launches of {args.kind} N={args.N} M={args.M} {args.dtype}"
-          f"{' adjoint' if args.adjoint else ''}")
+          f"{' adjoint' if args.adjoint else ''} {args.arith}")
 
 
 if __name__ == "__main__":

@@ -183,3 +183,89 @@ def test_rejects_host_pointer_and_bad_sizes(env):
     assert L.sb_solve_batched(fac.handle, dev.data_ptr(), dev.data_ptr(), 0, 8, 0, None) == sb.SB_OK
     # unknown dtype
     assert L.sb_solve_batched(fac.handle, dev.data_ptr(), dev.data_ptr(), 8, 8, 7, None) == sb.SB_ERR_INVALID_ARG
+
+
+# ------------------------------------------------ sb_solve_batched_ex / df32
+
+def run_ex(sb, torch, fac, rhs_host, M, rhs_dtype, x_dtype, arith, adjoint=False):
+    tin = torch.float64 if rhs_dtype == np.float64 else torch.float32
+    tout = torch.float64 if x_dtype == np.float64 else torch.float32
+    rhs = to_dev(rhs_host.astype(rhs_dtype), torch)
+    x = torch.full(rhs.shape, CANARY, dtype=tout, device="cuda")
+    sb.sb_solve_batched_ex(fac, rhs, x, transpose=adjoint, arith=arith, M=M, ld=rhs.shape[1])
+    torch.cuda.synchronize()
+    return to_host(x)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("kind", ["tri", "penta"])
+@pytest.mark.parametrize("N,M,ld", [(1, 3, 3), (2, 33, 40), (5, 100, 100), (130, 257, 260), (1024, 300, 301)])
+def test_df32_fp64_io_matches_oracle(env, kind, N, M, ld, adjoint):
+    sb, torch = env
+    if kind == "tri":
+        diags = synth.random_tri_diagonals(seed=40 + N, N=N)
+        fac = sb.sb_factor_shared_tri(*diags)
+        orc = oracle_tri
+    else:
+        diags = synth.random_penta_diagonals(seed=40 + N, N=N)
+        fac = sb.sb_factor_shared_penta(*diags)
+        orc = oracle_penta
+    rhs = synth.rhs_normal(seed=50 + N, N=N, M=M, ld=ld, pad_value=CANARY)
+    x = run_ex(sb, torch, fac, rhs, M, np.float64, np.float64, "df32", adjoint)
+    ref = orc(diags, rhs[:, :M], adjoint)
+    assert np.max(relerr_per_system(x[:, :M], ref)) <= TOL64
+    assert np.all(x[:, M:] == CANARY)
+
+
+@pytest.mark.parametrize("kind", ["tri", "penta"])
+def test_fp32_rhs_fp64_solution(env, kind):
+    """FP32-stored right-hand side solved into an FP64 solution: with df32
+    arithmetic to FP64 accuracy of the promoted input, with native FP32 to FP32
+    accuracy."""
+    sb, torch = env
+    N, M = 512, 1000
+    if kind == "tri":
+        diags = tuple(sb.sb_build_matrix("diffusion", N, 2.0))
+        fac = sb.sb_factor_shared_tri(*diags)
+        A = steppers.SharedTri(*matrices.diffusion_matrix(N, 2.0))
+    else:
+        diags = tuple(sb.sb_build_matrix("hinged", N, 0.25))
+        fac = sb.sb_factor_shared_penta(*diags)
+        A = steppers.SharedPenta(*matrices.hyperdiffusion_matrix(N, 0.25, "hinged"))
+    b32 = synth.rhs_uniform(seed=3, N=N, M=M, dtype=np.float32)
+    ref = steppers.solve_fp32_rhs(A, b32)
+    x = run_ex(sb, torch, fac, b32, M, np.float32, np.float64, "df32")
+    assert np.max(relerr_per_system(x, ref)) <= TOL64
+    x = run_ex(sb, torch, fac, b32, M, np.float32, np.float64, "native")
+    assert np.max(relerr_per_system(x, ref)) <= TOL32
+
+
+def test_workload_penta_df32_full_size_all_systems(env):
+    sb, torch = env
+    w = synth.WORKLOADS["penta_hyper"]
+    N, M = w["N"], w["M"]
+    fac = sb.sb_factor_shared_penta(*sb.sb_build_matrix("hinged", N, w["r"]))
+    rhs = synth.rhs_normal(seed=w["seed"], N=N, M=M)
+    x = run_ex(sb, torch, fac, rhs, M, np.float64, np.float64, "df32")
+    A = steppers.SharedPenta(*matrices.hyperdiffusion_matrix(N, w["r"], "hinged"))
+    err = relerr_per_system(x, A.solve(rhs))
+    assert np.max(err) <= TOL64, (np.max(err), np.median(err))
+
+
+def test_ex_rejects_unsupported_and_bad_alias(env):
+    sb, torch = env
+    N = 16
+    fac = sb.sb_factor_shared_tri(*synth.random_tri_diagonals(seed=1, N=N))
+    d64 = torch.zeros((N, 8), dtype=torch.float64, device="cuda")
+    d32 = torch.zeros((N, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(sb.SbError) as ei:   # FP64 rhs into FP32 x is not offered
+        sb.sb_solve_batched_ex(fac, d64, d32, arith="native")
+    assert ei.value.code == sb.SB_ERR_UNSUPPORTED
+    with pytest.raises(sb.SbError) as ei:   # df32 with FP32 output is not offered
+        sb.sb_solve_batched_ex(fac, d32, d32, arith="df32")
+    assert ei.value.code == sb.SB_ERR_UNSUPPORTED
+    L = sb.lib()
+    rc = L.sb_solve_batched_ex(fac.handle, 0, d32.data_ptr(), 1, d32.data_ptr(), 0, 8, 8, 0, None)
+    assert rc == sb.SB_ERR_INVALID_ARG and "alias" in sb.sb_last_error()
+    assert L.sb_solve_batched_ex(fac.handle, 2, d64.data_ptr(), 0, d64.data_ptr(), 0, 8, 8, 0, None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_solve_batched_ex(fac.handle, 0, d64.data_ptr(), 0, d64.data_ptr(), 0, 8, 8, 9, None) == sb.SB_ERR_INVALID_ARG
