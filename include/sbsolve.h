@@ -199,6 +199,58 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
 #define SB_MAT_CH_NOFLUX           4
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
 
+/*
+ * Implicit time steppers with a shared matrix (S4 + S10 of the hot path).
+ * One step solves  A C^{n+1} = B C^n + E (C^3 - C)^n  for every simulation:
+ *   SB_STEP_DIFFUSION      A = I + coef K, K = tridiag(-1, 2, -1) with Dirichlet rows.
+ *                          SB_SCHEME_BE: B = I (backward Euler, coef = r = dt/dx^2);
+ *                          SB_SCHEME_CN: B = I - coef K (section 3.2's Crank-Nicolson,
+ *                          coef = sigma = dt/(2 dx^2)).  bc must be SB_BC_DIRICHLET.
+ *   SB_STEP_HYPERDIFFUSION A = I + coef D4 with bc SB_BC_HINGED (D4 = D2 D2) or
+ *                          SB_BC_TRUNCATED (Toeplitz 1,-4,6,-4,1); B = I (BE) or
+ *                          I - coef D4 (section 4.2's Crank-Nicolson).
+ *   SB_STEP_CAHN_HILLIARD  section 5.1's semi-implicit scheme with no-flux ends
+ *                          (bc SB_BC_NOFLUX, scheme SB_SCHEME_BE): A = I + dt coef D4_N,
+ *                          B = I, E = dt D2_N, with coef = gamma in grid units (dx = 1).
+ * The stepper owns the factorised A and the right-hand-side coefficients.
+ */
+typedef struct sb_stepper sb_stepper;
+#define SB_STEP_DIFFUSION      1
+#define SB_STEP_HYPERDIFFUSION 2
+#define SB_STEP_CAHN_HILLIARD  3
+#define SB_SCHEME_BE 0
+#define SB_SCHEME_CN 1
+#define SB_BC_DIRICHLET 0
+#define SB_BC_HINGED    1
+#define SB_BC_TRUNCATED 2
+#define SB_BC_NOFLUX    3
+/* run modes: fused step kernel replayed from a captured CUDA graph (64 steps per
+ * graph; falls back to direct launches on the legacy NULL stream or while the
+ * stream is being captured), fused kernel launched directly, or the unfused
+ * reference pipeline (a separate right-hand-side kernel into `work`, then the
+ * batched solve) that mirrors the paper's two-kernel step. */
+#define SB_RUN_GRAPH   0
+#define SB_RUN_DIRECT  1
+#define SB_RUN_UNFUSED 2
+
+int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, double dt,
+                      sb_stepper** out);
+void sb_stepper_destroy(sb_stepper* st);
+/* The stepper's factor of A (owned by the stepper; valid until it is destroyed). */
+const sb_factor* sb_stepper_factor(const sb_stepper* st);
+/* Bytes of device workspace SB_RUN_UNFUSED needs for a (M, ld) batch. */
+int sb_stepper_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes);
+/*
+ * sb_stepper_run -- advance `state` (device FP64, N x ld interleaved, M simulations)
+ * by nsteps steps in place, asynchronously on `stream`.  arith as for
+ * sb_solve_batched_ex.  `work`/`work_bytes` are used only by SB_RUN_UNFUSED (the
+ * caller owns the workspace; NULL otherwise).  The first SB_RUN_GRAPH call for a
+ * given (state, M, ld, arith) captures and caches a graph: make that first call
+ * outside any stream capture of the caller's own.
+ */
+int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+                   int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char* sb_last_error(void);
 

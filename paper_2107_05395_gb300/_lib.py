@@ -71,6 +71,13 @@ SIGNATURES = {
     "sb_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _c_i64,
                                    _c_i64, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_float)]),
     "sb_build_matrix": (ctypes.c_int, [ctypes.c_int, _c_i64, ctypes.c_double, _dp]),
+    "sb_stepper_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i64, ctypes.c_double,
+                                         ctypes.c_double, ctypes.POINTER(_vp)]),
+    "sb_stepper_destroy": (None, [_vp]),
+    "sb_stepper_factor": (_vp, [_vp]),
+    "sb_stepper_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "sb_stepper_run": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, ctypes.c_int, _vp,
+                                      ctypes.c_size_t, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
 }
@@ -270,6 +277,59 @@ def sb_build_matrix(kind, N: int, coef: float):
     out = np.zeros((2 * P + 1) * N, dtype=np.float64)
     _check(lib().sb_build_matrix(code, N, float(coef), out.ctypes.data_as(_dp)))
     return tuple(out.reshape(2 * P + 1, N))
+
+
+STEP_KINDS = {"diffusion": 1, "hyperdiffusion": 2, "cahn_hilliard": 3}
+SCHEMES = {"be": 0, "cn": 1}
+BCS = {"dirichlet": 0, "hinged": 1, "truncated": 2, "noflux": 3}
+RUN_MODES = {"graph": 0, "direct": 1, "unfused": 2}
+
+
+class Stepper:
+    """Owns an sb_stepper (implicit time stepper with a shared, factorised matrix)."""
+
+    def __init__(self, kind, scheme, bc, N, coef, dt=0.0):
+        h = ctypes.c_void_p()
+        _check(lib().sb_stepper_create(STEP_KINDS[kind], SCHEMES[scheme], BCS[bc], int(N),
+                                       float(coef), float(dt), ctypes.byref(h)))
+        self.handle = h
+        self.kind, self.scheme, self.bc, self.N, self.coef, self.dt = kind, scheme, bc, N, coef, dt
+
+    def factor_handle(self):
+        return lib().sb_stepper_factor(self.handle)
+
+    def workspace_bytes(self, M, ld=None):
+        out = ctypes.c_size_t()
+        _check(lib().sb_stepper_workspace_bytes(self.handle, M, M if ld is None else ld, ctypes.byref(out)))
+        return out.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().sb_stepper_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sb_stepper_create(kind, scheme, bc, N, coef, dt=0.0) -> Stepper:
+    return Stepper(kind, scheme, bc, N, coef, dt)
+
+
+def sb_stepper_run(st: Stepper, state, nsteps, arith="native", mode="graph", work=None, M=None,
+                   ld=None, stream=None):
+    """Advance `state` ((N, ld) FP64 device tensor) by nsteps steps in place."""
+    M, ld = _batch_shape(state, st.N, M, ld)
+    wptr = 0 if work is None else _dev_ptr(work)
+    wbytes = 0 if work is None else (work.numel() * work.element_size() if not isinstance(work, int)
+                                     else st.workspace_bytes(M, ld))
+    _check(lib().sb_stepper_run(st.handle, _dev_ptr(state), M, ld, _arith_code(arith), int(nsteps),
+                                RUN_MODES[mode] if isinstance(mode, str) else int(mode), wptr or None,
+                                wbytes, _stream_handle(stream)))
+    return state
 
 
 def sb_last_error() -> str:

@@ -143,6 +143,11 @@ struct NativeArith {
   }
   static SB_HD S to_store(V v) { return v; }
   static SB_HD V from_store(S s) { return s; }
+  // value operations used to build right-hand sides
+  static SB_HD V add(V a, V b) { return a + b; }
+  static SB_HD V mulc(C c, V v) { return c * v; }
+  static SB_HD V fmac(C c, V v, V acc) { return std::fma(c, v, acc); }  // acc + c*v
+  static SB_HD V cubic(V c) { return std::fma(c * c, c, -c); }        // c^3 - c
 };
 
 // ---------------------------------------------------------- double-float
@@ -185,9 +190,9 @@ SB_HD df df_mul(df c, df v) {
 // compiler may if-convert them and issue their FP64 instructions (on GB300's slow
 // FP64 pipe) for every element, not only for the rare values that need them.
 #if defined(__CUDACC__)
-__host__ __device__ __noinline__
+static __host__ __device__ __noinline__
 #else
-inline
+static inline
 #endif
 df double_to_df_slow(double v) {
   const float h = (float)v;  // round to nearest, then the rest
@@ -215,12 +220,16 @@ SB_HD df double_to_df(double v) {
 
 // FP32 -> FP64 widening with integer operations only (exact): sign, exponent
 // re-biased by 1023 - 127 = 896, fraction shifted into the upper bits.  Zero and
-// FP32 subnormals give (signed) zero; infinities and NaNs are not expected here.
+// FP32 subnormals give (signed) zero; infinities stay infinite and NaNs NaN.
 SB_HD double widen_f32(float v) {
   const uint32_t b = f2u(v);
   const uint32_t mag = b & 0x7FFFFFFFu;
-  const uint32_t hi = (mag >= 0x00800000u) ? ((mag >> 3) + (896u << 20)) : 0u;
-  const uint32_t lo = (mag >= 0x00800000u) ? (b << 29) : 0u;
+  uint32_t hi = (mag >= 0x00800000u) ? ((mag >> 3) + (896u << 20)) : 0u;
+  uint32_t lo = (mag >= 0x00800000u) ? (b << 29) : 0u;
+  if (mag >= 0x7F800000u) {  // infinity or NaN
+    hi = (mag == 0x7F800000u) ? 0x7FF00000u : 0x7FF80000u;
+    lo = 0u;
+  }
   return hilo2d(hi | (b & 0x80000000u), lo);
 }
 
@@ -253,6 +262,26 @@ struct DFArith {
   }
   static SB_HD S to_store(V v) { return v; }
   static SB_HD V from_store(S s) { return s; }
+  // value operations used to build right-hand sides (all results normalised)
+  static SB_HD V add(V a, V b) {
+    const df s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, f_add(s.l, f_add(a.l, b.l)));
+  }
+  static SB_HD V mulc(C c, V v) {
+    const df p = df_mul(c, v);
+    return fast_two_sum(p.h, p.l);
+  }
+  static SB_HD V fmac(C c, V v, V acc) {  // acc + c*v
+    const df p = df_mul(c, v);
+    const df s = two_sum(acc.h, p.h);
+    return fast_two_sum(s.h, f_add(s.l, f_add(acc.l, p.l)));
+  }
+  static SB_HD V cubic(V c) {  // c^3 - c = c * (c*c - 1)
+    const df sq = mulc(c, c);
+    const df s = two_sum(sq.h, -1.0f);
+    const df q = fast_two_sum(s.h, f_add(s.l, sq.l));
+    return mulc(q, c);
+  }
 };
 
 }  // namespace sb

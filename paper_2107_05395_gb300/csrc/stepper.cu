@@ -1,0 +1,513 @@
+// Implicit time steppers with the shared matrix: diffusion and hyperdiffusion
+// (backward Euler or Crank-Nicolson, sections 3.2 and 4.2) and the semi-implicit
+// Cahn-Hilliard scheme of section 5.1.
+//
+// One step of every scheme is  A C^{n+1} = B C^n + E phi(C^n)  with band matrices
+// A (shared, factorised once), B (identity for backward Euler, I - sigma K for
+// Crank-Nicolson) and E (alpha D2_N for Cahn-Hilliard, phi(C) = C^3 - C).
+//
+// The fused kernel builds each right-hand-side row while the forward sweep
+// consumes it: a window of the state rows i-2 .. i+2 (and phi of rows i-1 .. i+1)
+// is kept in registers, fed by the same double-buffered row prefetch as the plain
+// sweep, so the step reads the state once and writes it once (the paper computes
+// the right-hand side with a separate stencil kernel every step).  Intermediates
+// go in place into the state array behind the window; the backward sweep then
+// overwrites them with C^{n+1}.  The time loop is captured into a CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "arith.cuh"
+#include "sb_internal.h"
+
+namespace sb {
+namespace {
+
+template <class A, typename T>
+struct StConv;
+template <>
+struct StConv<NativeArith<double>, double> {
+  static __device__ __forceinline__ double in(double v) { return v; }
+  static __device__ __forceinline__ double out(double v) { return v; }
+};
+template <>
+struct StConv<DFArith, double> {
+  static __device__ __forceinline__ df in(double v) { return double_to_df(v); }
+  static __device__ __forceinline__ double out(df v) { return df_to_double(v); }
+};
+
+// rcoef rows: if NB > 0, NB values per row (B at offsets -(NB/2)..NB/2), then if
+// HAS_E, 3 values per row (E at offsets -1..1).  Out-of-matrix entries are 0.
+template <class A, int P, int NB, bool HAS_E, int R>
+__global__ void __launch_bounds__(512)
+fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
+                  int N, int64_t M, int64_t ld, double* state, int64_t ntiles) {
+  using V = typename A::V;
+  using C = typename A::C;
+  using S = typename A::S;
+  constexpr int W = P + 1;
+  constexpr int NE = HAS_E ? 3 : 0;
+  constexpr int RW = NB + NE;  // rhs coefficients per row
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* cs = reinterpret_cast<C*>(smem_raw);
+  {
+    const int n = 2 * W * N;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
+    for (int k = threadIdx.x; k < RW * N; k += blockDim.x) cs[n + k] = rcoef[k];
+  }
+  __syncthreads();
+  const C* fw = cs;
+  const C* bw = cs + W * N;
+  const C* rc = cs + 2 * W * N;
+
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
+       tile += (int64_t)gridDim.x * nw) {
+    const int64_t m = tile * 32 + lane;
+    if (m >= M) continue;
+    double* y = state + m;
+
+    // window: cw[k] = C_{i-2+k}, pw[k] = phi(C_{i-1+k}) for the row i being built
+    V cw[5], pw[3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) cw[k] = A::zero();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pw[k] = A::zero();
+    double va[R], vb[R];
+    auto load_rows = [&](double (&buf)[R], int i0) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (i0 + j < N) buf[j] = y[(int64_t)(i0 + j) * ld];
+    };
+    // push raw row k (value v, already 0 when k >= N) into the windows
+    auto push = [&](double v) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cw[k] = cw[k + 1];
+      cw[4] = StConv<A, double>::in(v);
+      if constexpr (HAS_E) {
+        pw[0] = pw[1];
+        pw[1] = pw[2];
+        pw[2] = A::cubic(cw[3]);  // phi(C_{i+1}) once C_{i+1} entered the window
+      }
+    };
+    V u1 = A::zero(), u2 = A::zero();
+    auto build_and_sweep = [&](int i) {
+      V r;
+      if constexpr (NB > 0) {
+        const C* b = rc + RW * i;
+        r = A::mulc(b[0], cw[2 - NB / 2]);
+#pragma unroll
+        for (int k = 1; k < NB; ++k) r = A::fmac(b[k], cw[2 - NB / 2 + k], r);
+      } else {
+        r = cw[2];
+      }
+      if constexpr (HAS_E) {
+        const C* e = rc + RW * i + NB;
+        r = A::fmac(e[0], pw[0], r);
+        r = A::fmac(e[1], pw[1], r);
+        r = A::fmac(e[2], pw[2], r);
+      }
+      const V u = A::template step<P, false>(fw + W * i, r, u1, u2);
+      *reinterpret_cast<S*>(y + (int64_t)i * ld) = A::to_store(u);
+      u2 = u1;
+      u1 = u;
+    };
+    // prime: rows 0 and 1 enter the window before row 0 is built (rows -2, -1 are 0)
+    load_rows(va, 0);
+    load_rows(vb, R);
+    push(N > 0 ? va[0] : 0.0);
+    push(N > 1 ? va[1] : 0.0);
+    // row i needs raw row i + 2: from the current buffer or the next one
+    for (int i0 = 0; i0 < N; i0 += 2 * R) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int i = i0 + j;
+        if (i < N) {
+          const int k = j + 2;
+          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R]) : 0.0;
+          push(v);
+          build_and_sweep(i);
+        }
+      }
+      load_rows(va, i0 + 2 * R);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int i = i0 + R + j;
+        if (i < N) {
+          const int k = j + 2;
+          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R]) : 0.0;
+          push(v);
+          build_and_sweep(i);
+        }
+      }
+      load_rows(vb, i0 + 3 * R);
+    }
+
+    // backward sweep (B0 == 1 for the primal factors)
+    V x1 = A::zero(), x2 = A::zero();
+    S sa[R], sb_[R];
+    auto load_mid = [&](S (&buf)[R], int i0) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (i0 - j >= 0) buf[j] = *reinterpret_cast<const S*>(y + (int64_t)(i0 - j) * ld);
+    };
+    auto bwd = [&](S (&buf)[R], int i0) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int i = i0 - j;
+        if (i >= 0) {
+          const V xi = A::template step<P, true>(bw + W * i, A::from_store(buf[j]), x1, x2);
+          y[(int64_t)i * ld] = StConv<A, double>::out(xi);
+          x2 = x1;
+          x1 = xi;
+        }
+      }
+    };
+    load_mid(sa, N - 1);
+    for (int i0 = N - 1; i0 >= 0; i0 -= 2 * R) {
+      load_mid(sb_, i0 - R);
+      bwd(sa, i0);
+      load_mid(sa, i0 - 2 * R);
+      bwd(sb_, i0 - R);
+    }
+  }
+}
+
+// Unfused right-hand side (the paper's separate stencil pass): f = B C + E phi(C).
+template <class A, int NB, bool HAS_E>
+__global__ void rhs_kernel(const typename A::C* __restrict__ rcoef, int N, int64_t M, int64_t ld,
+                           const double* __restrict__ C_in, double* __restrict__ f) {
+  using V = typename A::V;
+  using C = typename A::C;
+  constexpr int RW = NB + (HAS_E ? 3 : 0);
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (m >= M || i >= N) return;
+  auto val = [&](int k) -> V {
+    return (k >= 0 && k < N) ? StConv<A, double>::in(C_in[(int64_t)k * ld + m]) : A::zero();
+  };
+  const C* row = rcoef + RW * i;
+  V r;
+  if constexpr (NB > 0) {
+    r = A::mulc(row[0], val(i - NB / 2));
+#pragma unroll
+    for (int k = 1; k < NB; ++k) r = A::fmac(row[k], val(i - NB / 2 + k), r);
+  } else {
+    r = val(i);
+  }
+  if constexpr (HAS_E) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r = A::fmac(row[NB + k], A::cubic(val(i - 1 + k)), r);
+  }
+  f[(int64_t)i * ld + m] = StConv<A, double>::out(r);
+}
+
+}  // namespace
+}  // namespace sb
+
+// ------------------------------------------------------------------ host side
+
+struct sb_stepper {
+  int kind = 0, scheme = 0, bc = 0;
+  int64_t N = 0;
+  double coef = 0.0, dt = 0.0;
+  sb_factor* fac = nullptr;
+  int NB = 0;            // B band width (0 = identity)
+  bool has_e = false;
+  double* r64 = nullptr;  // device rhs coefficient rows, FP64
+  float* rdf = nullptr;   // same as (hi, lo) pairs
+  std::mutex mu;
+  std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
+};
+
+namespace sb {
+namespace {
+
+constexpr int kStepRows = 8;
+constexpr int kGraphSteps = 64;  // steps per captured graph
+
+template <class A, int P, int NB, bool HAS_E>
+int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
+                 double* state, int64_t M, int64_t ld, cudaStream_t stream) {
+  const sb_factor* f = st->fac;
+  const int N = (int)f->N;
+  constexpr int RW = NB + (HAS_E ? 3 : 0);
+  const size_t smem = ((size_t)2 * (P + 1) * N + (size_t)RW * N) * sizeof(typename A::C);
+  if (smem > 227 * 1024)
+    return fail(SB_ERR_UNSUPPORTED, "N=%d too large for the fused step's shared memory", N);
+  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows>;
+  const int threads = 256;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> occ;
+  int nb = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(reinterpret_cast<const void*>(k), (int)smem);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem));
+      occ[key] = nb;
+    } else {
+      nb = it->second;
+    }
+  }
+  if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "fused step kernel cannot be resident");
+  const int64_t ntiles = (M + 31) / 32;
+  const int64_t want = (ntiles + threads / 32 - 1) / (threads / 32);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(f->device)));
+  k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, state, ntiles);
+  return cuda_check(cudaGetLastError(), "fused step launch");
+}
+
+template <class A, int NB, bool HAS_E>
+int launch_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, double* out,
+               int64_t M, int64_t ld, cudaStream_t stream) {
+  const int N = (int)st->N;
+  dim3 grid((unsigned)((M + 255) / 256), (unsigned)N);
+  rhs_kernel<A, NB, HAS_E><<<grid, 256, 0, stream>>>(rc, N, M, ld, in, out);
+  return cuda_check(cudaGetLastError(), "rhs launch");
+}
+
+template <class A>
+int one_step(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
+             double* state, int64_t M, int64_t ld, cudaStream_t stream) {
+  const int P = st->fac->P;
+  if (st->has_e) return launch_fused<A, 2, 0, true>(st, coef, rc, state, M, ld, stream);
+  if (P == 1)
+    return st->NB == 3 ? launch_fused<A, 1, 3, false>(st, coef, rc, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false>(st, coef, rc, state, M, ld, stream);
+  return st->NB == 5 ? launch_fused<A, 2, 5, false>(st, coef, rc, state, M, ld, stream)
+                     : launch_fused<A, 2, 0, false>(st, coef, rc, state, M, ld, stream);
+}
+
+template <class A>
+int one_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, double* out,
+            int64_t M, int64_t ld, cudaStream_t stream) {
+  if (st->has_e) return launch_rhs<A, 0, true>(st, rc, in, out, M, ld, stream);
+  if (st->NB == 3) return launch_rhs<A, 3, false>(st, rc, in, out, M, ld, stream);
+  if (st->NB == 5) return launch_rhs<A, 5, false>(st, rc, in, out, M, ld, stream);
+  return launch_rhs<A, 0, false>(st, rc, in, out, M, ld, stream);
+}
+
+int step_fused(const sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+               cudaStream_t stream) {
+  if (arith == SB_ARITH_DF32)
+    return one_step<DFArith>(st, reinterpret_cast<const df*>(st->fac->coefdf),
+                             reinterpret_cast<const df*>(st->rdf), state, M, ld, stream);
+  return one_step<NativeArith<double>>(st, st->fac->coef64, st->r64, state, M, ld, stream);
+}
+
+}  // namespace
+}  // namespace sb
+
+using namespace sb;
+
+extern "C" {
+
+int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, double dt,
+                      sb_stepper** out) {
+  clear_error();
+  if (!out) return fail(SB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 1) return fail(SB_ERR_INVALID_ARG, "N must be >= 1");
+  if (!std::isfinite(coef) || !std::isfinite(dt)) return fail(SB_ERR_INVALID_ARG, "non-finite coefficient");
+  int mat = 0;
+  double acoef = coef;
+  if (kind == SB_STEP_DIFFUSION) {
+    if (bc != SB_BC_DIRICHLET) return fail(SB_ERR_INVALID_ARG, "diffusion supports SB_BC_DIRICHLET");
+    mat = SB_MAT_DIFFUSION_DIRICHLET;
+  } else if (kind == SB_STEP_HYPERDIFFUSION) {
+    if (bc != SB_BC_HINGED && bc != SB_BC_TRUNCATED)
+      return fail(SB_ERR_INVALID_ARG, "hyperdiffusion supports SB_BC_HINGED or SB_BC_TRUNCATED");
+    mat = bc == SB_BC_HINGED ? SB_MAT_HYPER_HINGED : SB_MAT_HYPER_TRUNCATED;
+  } else if (kind == SB_STEP_CAHN_HILLIARD) {
+    if (bc != SB_BC_NOFLUX) return fail(SB_ERR_INVALID_ARG, "Cahn-Hilliard supports SB_BC_NOFLUX");
+    if (scheme != SB_SCHEME_BE)
+      return fail(SB_ERR_INVALID_ARG, "Cahn-Hilliard uses the semi-implicit scheme (SB_SCHEME_BE)");
+    if (!(dt > 0.0)) return fail(SB_ERR_INVALID_ARG, "dt must be > 0");
+    mat = SB_MAT_CH_NOFLUX;
+    acoef = dt * coef;
+  } else {
+    return fail(SB_ERR_INVALID_ARG, "unknown stepper kind %d", kind);
+  }
+  if (scheme != SB_SCHEME_BE && scheme != SB_SCHEME_CN)
+    return fail(SB_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+
+  std::vector<double> adiag;
+  int P = 0;
+  SB_TRY(build_matrix(mat, N, acoef, adiag, &P));
+  sb_stepper* st = new (std::nothrow) sb_stepper();
+  if (!st) return fail(SB_ERR_ALLOC, "host allocation failed");
+  st->kind = kind;
+  st->scheme = scheme;
+  st->bc = bc;
+  st->N = N;
+  st->coef = coef;
+  st->dt = dt;
+  int rc;
+  if (P == 1)
+    rc = sb_factor_shared_tri(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N, &st->fac);
+  else
+    rc = sb_factor_shared_penta(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N,
+                                adiag.data() + 3 * N, adiag.data() + 4 * N, &st->fac);
+  if (rc != SB_OK) {
+    delete st;
+    return rc;
+  }
+  // right-hand-side rows
+  std::vector<double> rows;
+  if (kind == SB_STEP_CAHN_HILLIARD) {
+    st->has_e = true;
+    rows.assign(3 * N, 0.0);  // dt * D2_N, cell-centred no-flux closure
+    for (int64_t i = 0; i < N; ++i) {
+      const bool first = (i == 0), last = (i == N - 1);
+      rows[3 * i + 0] = first ? 0.0 : dt;
+      rows[3 * i + 1] = dt * (-2.0 + (first ? 1.0 : 0.0) + (last ? 1.0 : 0.0));
+      rows[3 * i + 2] = last ? 0.0 : dt;
+    }
+  } else if (scheme == SB_SCHEME_CN) {
+    std::vector<double> bdiag;
+    int PB = 0;
+    rc = build_matrix(mat, N, -coef, bdiag, &PB);  // B = I - sigma K
+    if (rc != SB_OK) {
+      sb_stepper_destroy(st);
+      return rc;
+    }
+    st->NB = 2 * PB + 1;
+    rows.assign((size_t)st->NB * N, 0.0);
+    for (int64_t i = 0; i < N; ++i)
+      for (int k = 0; k < st->NB; ++k) rows[(size_t)st->NB * i + k] = bdiag[(size_t)k * N + i];
+  }
+  if (!rows.empty()) {
+    std::vector<float> rdf(2 * rows.size());
+    for (size_t k = 0; k < rows.size(); ++k) {
+      rdf[2 * k] = (float)rows[k];
+      rdf[2 * k + 1] = (float)(rows[k] - (double)rdf[2 * k]);
+    }
+    DeviceGuard g(st->fac->device);
+    rc = cuda_check(cudaMalloc(&st->r64, rows.size() * sizeof(double)), "cudaMalloc");
+    if (rc == SB_OK) rc = cuda_check(cudaMalloc(&st->rdf, rdf.size() * sizeof(float)), "cudaMalloc");
+    if (rc == SB_OK)
+      rc = cuda_check(cudaMemcpy(st->r64, rows.data(), rows.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (rc == SB_OK)
+      rc = cuda_check(cudaMemcpy(st->rdf, rdf.data(), rdf.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (rc != SB_OK) {
+      sb_stepper_destroy(st);
+      return rc;
+    }
+  }
+  *out = st;
+  return SB_OK;
+}
+
+void sb_stepper_destroy(sb_stepper* st) {
+  if (!st) return;
+  if (st->fac) {
+    DeviceGuard g(st->fac->device);
+    for (auto& kv : st->graphs) cudaGraphExecDestroy(kv.second);
+    if (st->r64) cudaFree(st->r64);
+    if (st->rdf) cudaFree(st->rdf);
+    sb_factor_destroy(st->fac);
+  }
+  delete st;
+}
+
+const sb_factor* sb_stepper_factor(const sb_stepper* st) { return st ? st->fac : nullptr; }
+
+int sb_stepper_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes) {
+  clear_error();
+  if (!st || !bytes) return fail(SB_ERR_INVALID_ARG, "NULL argument");
+  if (M < 0 || ld < M) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  *bytes = (size_t)((st->N - 1) * ld + M) * sizeof(double);
+  return SB_OK;
+}
+
+int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+                   int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream) {
+  clear_error();
+  if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
+  if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode %d", (int)arith);
+  if (mode != SB_RUN_GRAPH && mode != SB_RUN_DIRECT && mode != SB_RUN_UNFUSED)
+    return fail(SB_ERR_INVALID_ARG, "unknown run mode %d", mode);
+  const sb_factor* f = st->fac;
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  if (M < 0 || ld < M || ld < 1) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  if (M == 0 || nsteps == 0) return SB_OK;
+  const size_t bytes = (size_t)((f->N - 1) * ld + M) * sizeof(double);
+  SB_TRY(check_device_range(state, bytes, sizeof(double), f->device, "state"));
+  cudaStream_t s = (cudaStream_t)stream;
+
+  if (mode == SB_RUN_UNFUSED) {
+    if (work == nullptr || work_bytes < bytes)
+      return fail(SB_ERR_INVALID_ARG, "the unfused run needs a workspace of %zu bytes", bytes);
+    SB_TRY(check_device_range(work, bytes, sizeof(double), f->device, "work"));
+    SB_TRY(check_alias(state, bytes, work, bytes, "state", "work"));
+    double* w = static_cast<double*>(work);
+    for (int64_t n = 0; n < nsteps; ++n) {
+      if (st->NB == 0 && !st->has_e) {
+        SB_TRY(launch_sweep(f, OP_PRIMAL, state, SB_F64, state, SB_F64, M, ld, arith,
+                            shape_for(f, arith, SB_F64, SB_F64), s));
+        continue;
+      }
+      if (arith == SB_ARITH_DF32)
+        SB_TRY(one_rhs<DFArith>(st, reinterpret_cast<const df*>(st->rdf), state, w, M, ld, s));
+      else
+        SB_TRY(one_rhs<NativeArith<double>>(st, st->r64, state, w, M, ld, s));
+      SB_TRY(launch_sweep(f, OP_PRIMAL, w, SB_F64, state, SB_F64, M, ld, arith,
+                          shape_for(f, arith, SB_F64, SB_F64), s));
+    }
+    return SB_OK;
+  }
+
+  bool capturing = false;
+  if (mode == SB_RUN_GRAPH && s != nullptr) {
+    cudaStreamCaptureStatus cs;
+    SB_CUDA(cudaStreamIsCapturing(s, &cs));
+    capturing = (cs != cudaStreamCaptureStatusNone);
+  }
+  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
+    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(step_fused(st, state, M, ld, arith, s));
+    return SB_OK;
+  }
+  // graph of kGraphSteps fused steps, replayed; the remainder launched directly
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(st->mu);
+    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), M, ld, (int)arith, kGraphSteps);
+    auto it = st->graphs.find(key);
+    if (it != st->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t graph = nullptr;
+      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int rc = SB_OK;
+      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = step_fused(st, state, M, ld, arith, s);
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc != SB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      SB_CUDA(e);
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SB_CUDA(e);
+      st->graphs[key] = exec;
+    }
+  }
+  int64_t n = 0;
+  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
+  for (; n < nsteps; ++n) SB_TRY(step_fused(st, state, M, ld, arith, s));
+  return SB_OK;
+}
+
+}  // extern "C"
