@@ -200,6 +200,47 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
 
 /*
+ * Mixed precision with iterative refinement (S7 of the hot path): FP32 storage of
+ * the right-hand sides, FP32 sweeps with the FP64 factors rounded to FP32, and
+ * n_refine correction passes  r = b - A x,  d = A_32^{-1} r,  x += d  whose
+ * residual uses A's FP64 entries, evaluated in FP64 (residual_arith =
+ * SB_ARITH_NATIVE) or double-float (SB_ARITH_DF32).  The solution is FP64.
+ *
+ *   rhs        device FP32, N x ld interleaved;  x  device FP64, same layout
+ *              (must not overlap rhs).
+ *   n_refine   0..16 correction passes (0 = plain FP32 solve into FP64).
+ *   work       device workspace of sb_refine_workspace_bytes() bytes (FP32, one
+ *              element per solution element), owned by the caller; unused when
+ *              n_refine == 0 (may be NULL then).  Its contents are scratch.
+ * Each pass is one kernel: the residual is built from a window of x inside the
+ * forward sweep, so a pass reads b and x and writes x once (plus the workspace).
+ */
+int sb_refine_workspace_bytes(const sb_factor* f, int64_t M, int64_t ld, size_t* bytes);
+int sb_solve_batched_refined(const sb_factor* f, const float* rhs, double* x, int64_t M,
+                             int64_t ld, int n_refine, sb_arith residual_arith, void* work,
+                             size_t work_bytes, void* stream);
+
+/*
+ * sb_solve_batched_groups -- solve G (1..8) independent shared-LHS groups, each
+ * with its own factor (its own N) and batch, with one kernel launch per pass:
+ * the persistent CTAs are divided between the groups in proportion to N*M and
+ * each stages its own group's factors.  All factors of one call must have the
+ * same bandwidth and live on one device.
+ *   f, rhs, x, M, ld, work, work_bytes   arrays of G entries (work/work_bytes only
+ *                                        when n_refine > 0; may be NULL otherwise).
+ *   rhs_dtype, x_dtype, arith            as for sb_solve_batched_ex (n_refine == 0);
+ *                                        with n_refine > 0 they must be SB_F32,
+ *                                        SB_F64, SB_ARITH_NATIVE (FP32 sweeps).
+ *   residual_arith                       as for sb_solve_batched_refined.
+ * Passes: 1 + n_refine launches in total, whatever G is.
+ */
+int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const* rhs,
+                            void* const* x, const int64_t* M, const int64_t* ld,
+                            sb_dtype rhs_dtype, sb_dtype x_dtype, sb_arith arith, int n_refine,
+                            sb_arith residual_arith, void* const* work, const size_t* work_bytes,
+                            void* stream);
+
+/*
  * Implicit time steppers with a shared matrix (S4 + S10 of the hot path).
  * One step solves  A C^{n+1} = B C^n + E (C^3 - C)^n  for every simulation:
  *   SB_STEP_DIFFUSION      A = I + coef K, K = tridiag(-1, 2, -1) with Dirichlet rows.

@@ -71,6 +71,12 @@ SIGNATURES = {
     "sb_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _c_i64,
                                    _c_i64, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_float)]),
     "sb_build_matrix": (ctypes.c_int, [ctypes.c_int, _c_i64, ctypes.c_double, _dp]),
+    "sb_refine_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "sb_solve_batched_refined": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int,
+                                                _vp, ctypes.c_size_t, _vp]),
+    "sb_solve_batched_groups": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               _vp, _vp, _vp]),
     "sb_stepper_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i64, ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(_vp)]),
     "sb_stepper_destroy": (None, [_vp]),
@@ -277,6 +283,48 @@ def sb_build_matrix(kind, N: int, coef: float):
     out = np.zeros((2 * P + 1) * N, dtype=np.float64)
     _check(lib().sb_build_matrix(code, N, float(coef), out.ctypes.data_as(_dp)))
     return tuple(out.reshape(2 * P + 1, N))
+
+
+def sb_refine_workspace_bytes(f: Factor, M, ld=None):
+    out = ctypes.c_size_t()
+    _check(lib().sb_refine_workspace_bytes(f.handle, M, M if ld is None else ld, ctypes.byref(out)))
+    return out.value
+
+
+def _nbytes(t):
+    return 0 if t is None else (t.numel() * t.element_size())
+
+
+def sb_solve_batched_refined(f: Factor, rhs, x, n_refine=2, residual_arith="native", work=None,
+                             M=None, ld=None, stream=None):
+    """FP32 rhs -> FP64 x with FP32 sweeps and n_refine residual corrections."""
+    M, ld = _batch_shape(rhs, f.N, M, ld)
+    _check(lib().sb_solve_batched_refined(f.handle, _dev_ptr(rhs), _dev_ptr(x), M, ld, int(n_refine),
+                                          _arith_code(residual_arith),
+                                          None if work is None else _dev_ptr(work), _nbytes(work),
+                                          _stream_handle(stream)))
+    return x
+
+
+def sb_solve_batched_groups(factors, rhs, x, arith="native", n_refine=0, residual_arith="native",
+                            work=None, Ms=None, lds=None, stream=None):
+    """One launch per pass over several shared-LHS groups (lists of equal length)."""
+    G = len(factors)
+    shapes = [_batch_shape(rhs[g], factors[g].N, None if Ms is None else Ms[g],
+                           None if lds is None else lds[g]) for g in range(G)]
+    arr = lambda t, vals: (t * G)(*vals)
+    fa = arr(ctypes.c_void_p, [f.handle.value for f in factors])
+    ra = arr(ctypes.c_void_p, [_dev_ptr(t) for t in rhs])
+    xa = arr(ctypes.c_void_p, [_dev_ptr(t) for t in x])
+    Ma = arr(ctypes.c_int64, [s[0] for s in shapes])
+    la = arr(ctypes.c_int64, [s[1] for s in shapes])
+    wa = arr(ctypes.c_void_p, [0 if work is None else _dev_ptr(w) for w in (work or [None] * G)]) \
+        if work is not None else None
+    wb = arr(ctypes.c_size_t, [_nbytes(w) for w in work]) if work is not None else None
+    _check(lib().sb_solve_batched_groups(G, fa, ra, xa, Ma, la, _dtype_code(rhs[0], None),
+                                         _dtype_code(x[0], None), _arith_code(arith), int(n_refine),
+                                         _arith_code(residual_arith), wa, wb, _stream_handle(stream)))
+    return x
 
 
 STEP_KINDS = {"diffusion": 1, "hyperdiffusion": 2, "cahn_hilliard": 3}

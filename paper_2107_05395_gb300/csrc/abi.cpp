@@ -228,6 +228,21 @@ static int upload_factor(sb_factor* f) {
   SB_CUDA(cudaMemcpy(f->coef64, f->h_coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->coef32, c32.data(), nc * sizeof(float), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->diag64, f->h_diag.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
+  // row-major copy of A for residuals: arow[(2P+1)*i + k] = entry at offset k - P of row i
+  const int64_t nb = 2 * f->P + 1, N = f->N;
+  std::vector<double> arow((size_t)nb * N);
+  std::vector<float> arowdf(2 * (size_t)nb * N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t k = 0; k < nb; ++k) {
+      const double v = f->h_diag[(size_t)k * N + i];
+      arow[(size_t)nb * i + k] = v;
+      arowdf[2 * ((size_t)nb * i + k)] = (float)v;
+      arowdf[2 * ((size_t)nb * i + k) + 1] = (float)(v - (double)(float)v);
+    }
+  SB_CUDA(cudaMalloc(&f->arow64, arow.size() * sizeof(double)));
+  SB_CUDA(cudaMalloc(&f->arowdf, arowdf.size() * sizeof(float)));
+  SB_CUDA(cudaMemcpy(f->arow64, arow.data(), arow.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(f->arowdf, arowdf.data(), arowdf.size() * sizeof(float), cudaMemcpyHostToDevice));
   return SB_OK;
 }
 
@@ -239,6 +254,8 @@ static void free_factor(sb_factor* f) {
     if (f->coef32) cudaFree(f->coef32);
     if (f->coefdf) cudaFree(f->coefdf);
     if (f->diag64) cudaFree(f->diag64);
+    if (f->arow64) cudaFree(f->arow64);
+    if (f->arowdf) cudaFree(f->arowdf);
   }
   delete f;
 }

@@ -1,0 +1,483 @@
+// Mixed precision with iterative refinement and multi-group batching.
+//
+// Refinement (FP32 right-hand sides, FP64 solution):
+//   x_0 = sweep32(b);   for k = 1..n:  r = b - A x_{k-1} (FP64, or double-float),
+//                                      d = sweep32(r),  x_k = x_{k-1} + d.
+// The factorisation of A is the FP64 one rounded to FP32 for the sweeps; the
+// residual uses A's original FP64 entries.  Each refinement pass is one kernel:
+// its forward sweep builds r_i from a window of x (rows i-P .. i+P, prefetched
+// in batches) and writes the FP32 intermediate to a caller-provided workspace
+// (x must stay intact until every residual row is built); its backward sweep
+// adds d_i to x_i.
+//
+// Groups: several shared-LHS factors (different N) are solved by one launch per
+// pass.  The persistent CTAs are split between the groups in proportion to
+// N*M; a CTA stages its own group's coefficients once.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "sb_internal.h"
+#include "sweep_tile.cuh"
+
+namespace sb {
+namespace {
+
+constexpr int kMaxGroups = 8;
+
+template <typename CT, typename TI, typename TO>
+struct Groups {
+  int G;
+  int cta_begin[kMaxGroups + 1];
+  const CT* coef[kMaxGroups];   // sweep rows [forward | backward]
+  const void* arow[kMaxGroups]; // A row by row (refinement passes only)
+  int N[kMaxGroups];
+  int64_t M[kMaxGroups], ld[kMaxGroups], ntiles[kMaxGroups];
+  const TI* rhs[kMaxGroups];
+  TO* x[kMaxGroups];
+  float* work[kMaxGroups];
+};
+
+__device__ __forceinline__ int group_of(const int* cta_begin, int G) {
+  int g = 0;
+  while (g + 1 < G && (int)blockIdx.x >= cta_begin[g + 1]) ++g;
+  return g;
+}
+
+// ---------------------------------------------------------- grouped sweep
+
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO>
+__global__ void __launch_bounds__(512)
+grouped_sweep_kernel(const __grid_constant__ Groups<typename A::C, TI, TO> a) {
+  using C = typename A::C;
+  constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* cs = reinterpret_cast<C*>(smem_raw);
+  const int g = group_of(a.cta_begin, a.G);
+  const int N = a.N[g];
+  stage(cs, a.coef[g], 2 * W * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
+  for (int64_t tile = (int64_t)(blockIdx.x - a.cta_begin[g]) * nw + (threadIdx.x >> 5);
+       tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
+    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, 1, kRows>(cs, cs + W * N, N, a.M[g], a.ld[g],
+                                                     a.rhs[g], a.x[g], tile);
+}
+
+// ------------------------------------------------------- refinement pass
+
+// FP64 -> FP32 by truncation with integer operations (the sign, exponent and top
+// 23 fraction bits); exact FP64 conversion outside the integer path's range.
+__device__ __forceinline__ float narrow_trunc(double v) { return double_to_df(v).h; }
+
+template <bool DFRES>
+struct Residual;
+
+template <>
+struct Residual<false> {  // FP64 residual: r = b - sum_k a_k x_{i+k} with FMAs
+  using X = double;
+  using AC = double;
+  static __device__ __forceinline__ X in(double v) { return v; }
+  template <int NB>
+  static __device__ __forceinline__ float eval(const AC* a, const X* xw, float b) {
+    double r = widen_f32(b);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) r = fma(-a[k], xw[k], r);
+    return narrow_trunc(r);
+  }
+};
+
+template <>
+struct Residual<true> {  // the same residual in double-float arithmetic
+  using X = df;
+  using AC = df;
+  static __device__ __forceinline__ X in(double v) { return double_to_df(v); }
+  template <int NB>
+  static __device__ __forceinline__ float eval(const AC* a, const X* xw, float b) {
+    df r = {b, 0.f};
+#pragma unroll
+    for (int k = 0; k < NB; ++k) r = DFArith::fmac(df{-a[k].h, -a[k].l}, xw[k], r);
+    return r.h;
+  }
+};
+
+template <int P, bool DFRES, int R>
+__device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
+                                            const typename Residual<DFRES>::AC* arow, int N,
+                                            int64_t M, int64_t ld, const float* b, double* x,
+                                            float* g, int64_t tile) {
+  using RS = Residual<DFRES>;
+  using X = typename RS::X;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const float* bp = b + m;
+  double* xp = x + m;
+  float* gp = g + m;
+
+  // ---- forward: r_i = b_i - (A x)_i, FP32 forward sweep, intermediate to g
+  X xw[NB];  // x_{i-P} .. x_{i+P}
+#pragma unroll
+  for (int k = 0; k < NB; ++k) xw[k] = RS::in(0.0);
+  double xa[R], xb[R];
+  float ba[R], bb[R];
+  auto load = [&](double (&xs)[R], float (&bs)[R], int i0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (i0 + j < N) {
+        xs[j] = xp[(int64_t)(i0 + j) * ld];
+        bs[j] = ld_stream(bp + (int64_t)(i0 + j) * ld);
+      }
+  };
+  auto push = [&](double v) {
+#pragma unroll
+    for (int k = 0; k < NB - 1; ++k) xw[k] = xw[k + 1];
+    xw[NB - 1] = RS::in(v);
+  };
+  float u1 = 0.f, u2 = 0.f;
+  auto row = [&](int i, float bi) {
+    const float r = RS::template eval<NB>(arow + NB * i, xw, bi);
+    const float u = NativeArith<float>::step<P, false>(fw + W * i, r, u1, u2);
+    gp[(int64_t)i * ld] = u;
+    u2 = u1;
+    u1 = u;
+  };
+  load(xa, ba, 0);
+  load(xb, bb, R);
+#pragma unroll
+  for (int k = 0; k < P; ++k) push(k < N ? xa[k] : 0.0);  // rows 0 .. P-1 enter first
+  for (int i0 = 0; i0 < N; i0 += 2 * R) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = i0 + j;
+      if (i < N) {
+        const int k = j + P;
+        push(i + P < N ? (k < R ? xa[k] : xb[k - R]) : 0.0);
+        row(i, ba[j]);
+      }
+    }
+    load(xa, ba, i0 + 2 * R);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = i0 + R + j;
+      if (i < N) {
+        const int k = j + P;
+        push(i + P < N ? (k < R ? xb[k] : xa[k - R]) : 0.0);
+        row(i, bb[j]);
+      }
+    }
+    load(xb, bb, i0 + 3 * R);
+  }
+
+  // ---- backward: FP32 back sweep of g, x_i += d_i
+  float d1 = 0.f, d2 = 0.f;
+  float ga[R], gb[R];
+  double ya[R], yb[R];
+  auto loadb = [&](float (&gs)[R], double (&ys)[R], int i0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (i0 - j >= 0) {
+        gs[j] = gp[(int64_t)(i0 - j) * ld];
+        ys[j] = xp[(int64_t)(i0 - j) * ld];
+      }
+  };
+  auto bwd = [&](float (&gs)[R], double (&ys)[R], int i0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = i0 - j;
+      if (i >= 0) {
+        const float d = NativeArith<float>::step<P, true>(bw + W * i, gs[j], d1, d2);
+        st_stream(xp + (int64_t)i * ld, ys[j] + widen_f32(d));
+        d2 = d1;
+        d1 = d;
+      }
+    }
+  };
+  loadb(ga, ya, N - 1);
+  for (int i0 = N - 1; i0 >= 0; i0 -= 2 * R) {
+    loadb(gb, yb, i0 - R);
+    bwd(ga, ya, i0);
+    loadb(ga, ya, i0 - 2 * R);
+    bwd(gb, yb, i0 - R);
+  }
+}
+
+template <int P, bool DFRES>
+__global__ void __launch_bounds__(512)
+grouped_refine_kernel(const __grid_constant__ Groups<float, float, double> a) {
+  using AC = typename Residual<DFRES>::AC;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = group_of(a.cta_begin, a.G);
+  const int N = a.N[g];
+  AC* as = reinterpret_cast<AC*>(smem_raw);  // A rows first (8-byte aligned)
+  float* cs = reinterpret_cast<float*>(as + NB * N);
+  stage(as, static_cast<const AC*>(a.arow[g]), NB * N);
+  stage(cs, a.coef[g], 2 * W * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
+  for (int64_t tile = (int64_t)(blockIdx.x - a.cta_begin[g]) * nw + (threadIdx.x >> 5);
+       tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
+    refine_tile<P, DFRES, kRows>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g],
+                                 a.work[g], tile);
+}
+
+// ------------------------------------------------------------------ host
+
+constexpr int kThreads = 256;
+
+template <typename K>
+int resident_ctas(K kernel, int device, size_t smem, int* total) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  int nb = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(reinterpret_cast<const void*>(kernel), smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      nb = it->second;
+    } else {
+      SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem));
+      cache[key] = nb;
+    }
+  }
+  if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "grouped kernel cannot be resident (%zu B smem)", smem);
+  *total = nb * sm_count(device);
+  return SB_OK;
+}
+
+// Splits `total` CTAs over the groups in proportion to N*M (each group gets at
+// least one CTA and no more than it has tiles for).  Returns the grid size.
+template <typename GA>
+int plan(GA& a, const std::vector<const sb_factor*>& f, int total) {
+  const int nw = kThreads / 32;
+  double work = 0.0;
+  for (int g = 0; g < a.G; ++g) work += (double)f[g]->N * (double)a.M[g];
+  int begin = 0;
+  for (int g = 0; g < a.G; ++g) {
+    const int64_t need = (a.ntiles[g] + nw - 1) / nw;
+    int64_t share = (int64_t)std::llround(total * ((double)f[g]->N * (double)a.M[g]) / work);
+    share = std::max<int64_t>(1, std::min<int64_t>(share, need));
+    a.cta_begin[g] = begin;
+    begin += (int)share;
+  }
+  a.cta_begin[a.G] = begin;
+  return begin;
+}
+
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO>
+int launch_grouped_sweep(const std::vector<const sb_factor*>& f, Op op,
+                         const std::vector<const void*>& rhs, const std::vector<void*>& x,
+                         const std::vector<int64_t>& M, const std::vector<int64_t>& ld,
+                         const typename A::C* const* coefs, cudaStream_t stream) {
+  using C = typename A::C;
+  Groups<C, TI, TO> a{};
+  a.G = (int)f.size();
+  size_t smem = 0;
+  for (int g = 0; g < a.G; ++g) {
+    a.coef[g] = coefs[g] + (op == OP_PRIMAL ? 0 : op_block_len(P, f[g]->N));
+    a.N[g] = (int)f[g]->N;
+    a.M[g] = M[g];
+    a.ld[g] = ld[g];
+    a.ntiles[g] = (M[g] + 31) / 32;
+    a.rhs[g] = static_cast<const TI*>(rhs[g]);
+    a.x[g] = static_cast<TO*>(x[g]);
+    smem = std::max(smem, (size_t)2 * (P + 1) * f[g]->N * sizeof(C));
+  }
+  if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
+  auto k = grouped_sweep_kernel<A, P, F_ONE, B_ONE, TI, TO>;
+  int total = 0;
+  SB_TRY(resident_ctas(k, f[0]->device, smem, &total));
+  const int grid = plan(a, f, total);
+  k<<<grid, kThreads, smem, stream>>>(a);
+  return cuda_check(cudaGetLastError(), "grouped sweep launch");
+}
+
+template <int P, bool DFRES>
+int launch_grouped_refine(const std::vector<const sb_factor*>& f, const std::vector<const void*>& rhs,
+                          const std::vector<void*>& x, const std::vector<int64_t>& M,
+                          const std::vector<int64_t>& ld, const std::vector<void*>& work,
+                          cudaStream_t stream) {
+  using AC = typename Residual<DFRES>::AC;
+  Groups<float, float, double> a{};
+  a.G = (int)f.size();
+  size_t smem = 0;
+  for (int g = 0; g < a.G; ++g) {
+    a.coef[g] = f[g]->coef32;  // primal block
+    a.arow[g] = DFRES ? static_cast<const void*>(f[g]->arowdf) : static_cast<const void*>(f[g]->arow64);
+    a.N[g] = (int)f[g]->N;
+    a.M[g] = M[g];
+    a.ld[g] = ld[g];
+    a.ntiles[g] = (M[g] + 31) / 32;
+    a.rhs[g] = static_cast<const float*>(rhs[g]);
+    a.x[g] = static_cast<double*>(x[g]);
+    a.work[g] = static_cast<float*>(work[g]);
+    smem = std::max(smem, (size_t)(2 * P + 1) * f[g]->N * sizeof(AC) +
+                              (size_t)2 * (P + 1) * f[g]->N * sizeof(float));
+  }
+  if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
+  auto k = grouped_refine_kernel<P, DFRES>;
+  int total = 0;
+  SB_TRY(resident_ctas(k, f[0]->device, smem, &total));
+  const int grid = plan(a, f, total);
+  k<<<grid, kThreads, smem, stream>>>(a);
+  return cuda_check(cudaGetLastError(), "refinement pass launch");
+}
+
+template <class A, typename TI, typename TO>
+int grouped_sweep_dispatch(const std::vector<const sb_factor*>& f, Op op,
+                           const std::vector<const void*>& rhs, const std::vector<void*>& x,
+                           const std::vector<int64_t>& M, const std::vector<int64_t>& ld,
+                           const typename A::C* const* coefs, cudaStream_t s) {
+  if (f[0]->P == 1)
+    return op == OP_PRIMAL
+               ? launch_grouped_sweep<A, 1, false, true, TI, TO>(f, op, rhs, x, M, ld, coefs, s)
+               : launch_grouped_sweep<A, 1, true, false, TI, TO>(f, op, rhs, x, M, ld, coefs, s);
+  return op == OP_PRIMAL
+             ? launch_grouped_sweep<A, 2, false, true, TI, TO>(f, op, rhs, x, M, ld, coefs, s)
+             : launch_grouped_sweep<A, 2, true, false, TI, TO>(f, op, rhs, x, M, ld, coefs, s);
+}
+
+size_t dsize(sb_dtype t) { return t == SB_F64 ? 8 : (t == SB_F32 ? 4 : 0); }
+
+}  // namespace
+
+int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void* const* x,
+                 const int64_t* M, const int64_t* ld, sb_dtype rt, sb_dtype xt, sb_arith arith,
+                 int n_refine, sb_arith res_arith, void* const* work, const size_t* work_bytes,
+                 cudaStream_t stream) {
+  if (G < 1 || G > kMaxGroups)
+    return fail(SB_ERR_INVALID_ARG, "number of groups must be in [1, %d]", kMaxGroups);
+  if (!fs || !rhs || !x || !M || !ld) return fail(SB_ERR_INVALID_ARG, "NULL array argument");
+  if (n_refine < 0 || n_refine > 16) return fail(SB_ERR_INVALID_ARG, "n_refine must be in [0, 16]");
+  if (dsize(rt) == 0 || dsize(xt) == 0) return fail(SB_ERR_INVALID_ARG, "unknown dtype");
+  if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode");
+  if (res_arith != SB_ARITH_NATIVE && res_arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown residual arithmetic mode");
+  std::vector<const sb_factor*> f;
+  std::vector<const void*> r;
+  std::vector<void*> xs, ws;
+  std::vector<int64_t> Ms, lds;
+  for (int g = 0; g < G; ++g) {
+    if (!fs[g]) return fail(SB_ERR_INVALID_ARG, "factor %d is NULL", g);
+    if (fs[g]->P != fs[0]->P)
+      return fail(SB_ERR_UNSUPPORTED, "all groups of one call must have the same bandwidth");
+    if (fs[g]->device != fs[0]->device)
+      return fail(SB_ERR_INVALID_ARG, "all groups of one call must live on one device");
+    if (M[g] < 1 || ld[g] < M[g])
+      return fail(SB_ERR_INVALID_ARG, "group %d: need M >= 1 and ld >= M", g);
+    if (ld[g] > ((int64_t)1 << 40) / fs[g]->N) return fail(SB_ERR_INVALID_ARG, "N*ld too large");
+    const size_t elems = (size_t)((fs[g]->N - 1) * ld[g] + M[g]);
+    SB_TRY(check_device_range(rhs[g], elems * dsize(rt), dsize(rt), fs[g]->device, "rhs"));
+    SB_TRY(check_device_range(x[g], elems * dsize(xt), dsize(xt), fs[g]->device, "x"));
+    if (rhs[g] == x[g] && rt != xt) return fail(SB_ERR_INVALID_ARG, "x may alias rhs only with equal dtypes");
+    SB_TRY(check_alias(rhs[g], elems * dsize(rt), x[g], elems * dsize(xt), "rhs", "x"));
+    if (n_refine > 0) {
+      if (!work || !work_bytes || !work[g] || work_bytes[g] < elems * sizeof(float))
+        return fail(SB_ERR_INVALID_ARG, "group %d: refinement needs a workspace of %zu bytes", g,
+                    elems * sizeof(float));
+      SB_TRY(check_device_range(work[g], elems * sizeof(float), 4, fs[g]->device, "work"));
+      SB_TRY(check_alias(work[g], elems * sizeof(float), x[g], elems * dsize(xt), "work", "x"));
+      SB_TRY(check_alias(work[g], elems * sizeof(float), rhs[g], elems * dsize(rt), "work", "rhs"));
+      ws.push_back(work[g]);
+    }
+    f.push_back(fs[g]);
+    r.push_back(rhs[g]);
+    xs.push_back(x[g]);
+    Ms.push_back(M[g]);
+    lds.push_back(ld[g]);
+  }
+  if (n_refine > 0 && (rt != SB_F32 || xt != SB_F64 || arith != SB_ARITH_NATIVE))
+    return fail(SB_ERR_UNSUPPORTED,
+                "refinement takes FP32 right-hand sides, FP64 solutions and FP32 sweeps (native)");
+  if (n_refine > 0)
+    for (int g = 0; g < G; ++g)
+      if (rhs[g] == x[g]) return fail(SB_ERR_INVALID_ARG, "refinement needs x separate from rhs");
+
+  DeviceGuard dg(f[0]->device);
+  SB_TRY(dg.rc);
+  std::vector<const float*> c32(G);
+  std::vector<const double*> c64(G);
+  std::vector<const df*> cdf(G);
+  for (int g = 0; g < G; ++g) {
+    c32[g] = f[g]->coef32;
+    c64[g] = f[g]->coef64;
+    cdf[g] = reinterpret_cast<const df*>(f[g]->coefdf);
+  }
+  // first pass (the whole solve when n_refine == 0)
+  int rc;
+  if (arith == SB_ARITH_DF32) {
+    if (rt == SB_F64 && xt == SB_F64)
+      rc = grouped_sweep_dispatch<DFArith, double, double>(f, OP_PRIMAL, r, xs, Ms, lds, cdf.data(), stream);
+    else if (rt == SB_F32 && xt == SB_F64)
+      rc = grouped_sweep_dispatch<DFArith, float, double>(f, OP_PRIMAL, r, xs, Ms, lds, cdf.data(), stream);
+    else
+      rc = fail(SB_ERR_UNSUPPORTED, "double-float sweeps write FP64 solutions");
+  } else if (rt == SB_F64 && xt == SB_F64) {
+    rc = grouped_sweep_dispatch<NativeArith<double>, double, double>(f, OP_PRIMAL, r, xs, Ms, lds, c64.data(), stream);
+  } else if (rt == SB_F32 && xt == SB_F32) {
+    rc = grouped_sweep_dispatch<NativeArith<float>, float, float>(f, OP_PRIMAL, r, xs, Ms, lds, c32.data(), stream);
+  } else if (rt == SB_F32 && xt == SB_F64) {
+    rc = grouped_sweep_dispatch<NativeArith<float>, float, double>(f, OP_PRIMAL, r, xs, Ms, lds, c32.data(), stream);
+  } else {
+    rc = fail(SB_ERR_UNSUPPORTED, "unsupported dtype combination");
+  }
+  SB_TRY(rc);
+  for (int k = 0; k < n_refine; ++k) {
+    if (f[0]->P == 1)
+      rc = res_arith == SB_ARITH_DF32 ? launch_grouped_refine<1, true>(f, r, xs, Ms, lds, ws, stream)
+                                      : launch_grouped_refine<1, false>(f, r, xs, Ms, lds, ws, stream);
+    else
+      rc = res_arith == SB_ARITH_DF32 ? launch_grouped_refine<2, true>(f, r, xs, Ms, lds, ws, stream)
+                                      : launch_grouped_refine<2, false>(f, r, xs, Ms, lds, ws, stream);
+    SB_TRY(rc);
+  }
+  return SB_OK;
+}
+
+}  // namespace sb
+
+using namespace sb;
+
+extern "C" {
+
+int sb_refine_workspace_bytes(const sb_factor* f, int64_t M, int64_t ld, size_t* bytes) {
+  clear_error();
+  if (!f || !bytes) return fail(SB_ERR_INVALID_ARG, "NULL argument");
+  if (M < 0 || ld < M) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  *bytes = M == 0 ? 0 : (size_t)((f->N - 1) * ld + M) * sizeof(float);
+  return SB_OK;
+}
+
+int sb_solve_batched_refined(const sb_factor* f, const float* rhs, double* x, int64_t M,
+                             int64_t ld, int n_refine, sb_arith residual_arith, void* work,
+                             size_t work_bytes, void* stream) {
+  clear_error();
+  if (!f) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  if (M == 0) return SB_OK;
+  const void* r = rhs;
+  void* xx = x;
+  return solve_groups(1, &f, &r, &xx, &M, &ld, SB_F32, SB_F64, SB_ARITH_NATIVE, n_refine,
+                      residual_arith, &work, &work_bytes, (cudaStream_t)stream);
+}
+
+int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const* rhs,
+                            void* const* x, const int64_t* M, const int64_t* ld,
+                            sb_dtype rhs_dtype, sb_dtype x_dtype, sb_arith arith, int n_refine,
+                            sb_arith residual_arith, void* const* work, const size_t* work_bytes,
+                            void* stream) {
+  clear_error();
+  return solve_groups(G, f, rhs, x, M, ld, rhs_dtype, x_dtype, arith, n_refine, residual_arith,
+                      work, work_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -64,6 +64,8 @@ struct sb_factor {
   float* coef32 = nullptr;   // device: same values rounded to FP32
   float* coefdf = nullptr;   // device: same values as (hi, lo) FP32 pairs
   double* diag64 = nullptr;  // device: the original 2P+1 diagonals, diagonal-major (d * N + i)
+  double* arow64 = nullptr;  // device: A row by row, (2P+1) entries per row (offsets -P..P)
+  float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64
 };

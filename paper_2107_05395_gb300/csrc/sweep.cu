@@ -16,157 +16,28 @@
 #include <mutex>
 #include <unordered_map>
 
-#include "arith.cuh"
 #include "sb_internal.h"
+#include "sweep_tile.cuh"
 
 namespace sb {
 namespace {
 
-constexpr int kRows = 8;  // rows per prefetch batch
-
-// ------------------------------------------------------------ conversions
-
-template <class A, typename T>
-struct Conv;
-
-template <typename T>
-struct Conv<NativeArith<T>, T> {
-  static __device__ __forceinline__ T in(T v) { return v; }
-  static __device__ __forceinline__ T out(T v) { return v; }
-};
-template <>
-struct Conv<NativeArith<float>, double> {  // FP32 arithmetic, FP64 output
-  static __device__ __forceinline__ double out(float v) { return (double)v; }
-};
-template <>
-struct Conv<DFArith, double> {
-  static __device__ __forceinline__ df in(double v) { return double_to_df(v); }
-  static __device__ __forceinline__ double out(df v) { return df_to_double(v); }
-};
-template <>
-struct Conv<DFArith, float> {
-  static __device__ __forceinline__ df in(float v) { return {v, 0.f}; }
-};
-
-template <typename T>
-__device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
-template <typename T>
-__device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
-
-// ------------------------------------------------------------------ kernel
-
-// coef: [forward rows][backward rows], (P + 1) coefficients per row:
-//   forward  u_i = F0 r_i - F1 u_{i-1} - F2 u_{i-2}      (F0 == 1 when F_ONE)
-//   backward x_i = B0 u_i - B1 x_{i+1} - B2 x_{i+2}      (B0 == 1 when B_ONE)
-// SPT systems per thread (m and m + 32, ... within a tile of 32*SPT systems) give
-// each thread SPT independent recurrences to interleave; R rows per prefetch batch.
+// Single-factor kernel: persistent CTAs stage the coefficients once, then their
+// warps take tiles round-robin over the grid.
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
 __global__ void __launch_bounds__(512)
 sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld,
              const TI* rhs, TO* x, int64_t ntiles) {
-  using V = typename A::V;
   using C = typename A::C;
-  using S = typename A::S;
-  static_assert(sizeof(S) <= sizeof(TO), "intermediate must fit in an output element");
   constexpr int W = P + 1;
-
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cs = reinterpret_cast<C*>(smem_raw);
-  {
-    const int n = 2 * W * N;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
-  }
+  stage(cs, coef, 2 * W * N);
   __syncthreads();
-  const C* fw = cs;
-  const C* bw = cs + W * N;
-
-  const int lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
-       tile += (int64_t)gridDim.x * nw) {
-    const int64_t m0 = tile * (32 * SPT) + lane;
-    if (m0 >= M) continue;
-    bool ok[SPT];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) ok[s] = (m0 + 32 * s) < M;
-    const TI* r = rhs + m0;
-    TO* y = x + m0;
-    auto slot = [&](int i, int s) {
-      return reinterpret_cast<S*>(y + (int64_t)i * ld + 32 * s);
-    };
-
-    // ---- forward sweep
-    V u1[SPT], u2[SPT];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = A::zero();
-    TI va[R][SPT], vb[R][SPT];
-    auto load_in = [&](TI (&buf)[R][SPT], int i0) {
-#pragma unroll
-      for (int j = 0; j < R; ++j)
-#pragma unroll
-        for (int s = 0; s < SPT; ++s)
-          if (i0 + j < N && ok[s]) buf[j][s] = ld_stream(r + (int64_t)(i0 + j) * ld + 32 * s);
-    };
-    auto fwd = [&](TI (&buf)[R][SPT], int i0) {
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int i = i0 + j;
-        if (i < N) {
-          const C* c = fw + W * i;
-#pragma unroll
-          for (int s = 0; s < SPT; ++s) {
-            const V u = A::template step<P, F_ONE>(c, Conv<A, TI>::in(buf[j][s]), u1[s], u2[s]);
-            if (ok[s]) *slot(i, s) = A::to_store(u);
-            u2[s] = u1[s];
-            u1[s] = u;
-          }
-        }
-      }
-    };
-    load_in(va, 0);
-    for (int i0 = 0; i0 < N; i0 += 2 * R) {
-      load_in(vb, i0 + R);
-      fwd(va, i0);
-      load_in(va, i0 + 2 * R);
-      fwd(vb, i0 + R);
-    }
-
-    // ---- backward sweep
-    V x1[SPT], x2[SPT];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = A::zero();
-    S sa[R][SPT], sb_[R][SPT];
-    auto load_mid = [&](S (&buf)[R][SPT], int i0) {
-#pragma unroll
-      for (int j = 0; j < R; ++j)
-#pragma unroll
-        for (int s = 0; s < SPT; ++s)
-          if (i0 - j >= 0 && ok[s]) buf[j][s] = *slot(i0 - j, s);
-    };
-    auto bwd = [&](S (&buf)[R][SPT], int i0) {
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int i = i0 - j;
-        if (i >= 0) {
-          const C* c = bw + W * i;
-#pragma unroll
-          for (int s = 0; s < SPT; ++s) {
-            const V xi = A::template step<P, B_ONE>(c, A::from_store(buf[j][s]), x1[s], x2[s]);
-            if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(xi));
-            x2[s] = x1[s];
-            x1[s] = xi;
-          }
-        }
-      }
-    };
-    load_mid(sa, N - 1);
-    for (int i0 = N - 1; i0 >= 0; i0 -= 2 * R) {
-      load_mid(sb_, i0 - R);
-      bwd(sa, i0);
-      load_mid(sa, i0 - 2 * R);
-      bwd(sb_, i0 - R);
-    }
-  }
+       tile += (int64_t)gridDim.x * nw)
+    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R>(cs, cs + W * N, N, M, ld, rhs, x, tile);
 }
 
 // ----------------------------------------------------------------- launching

@@ -1,0 +1,120 @@
+"""GPU parity of the mixed-precision refinement and the multi-group launch.
+
+Reference: the FP64 oracle applied to the FP32 right-hand side promoted exactly to
+FP64.  Bounds: a plain FP32 solve is FP32-accurate (2e-5); each refinement pass
+must shrink the error; after two passes the error is below 1e-10 (the refined-path
+target).  The multi-group workload (N = 128 / 512 / 2048, r = 0.1 / 0.5 / 2.0,
+2^21 right-hand sides split 4:2:1, two refinements, one call) is checked per
+group on systems sampled across each batch."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import banded, matrices, steppers
+from tests.gpu_util import lib_or_skip, relerr_per_system, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_or_skip()
+
+
+def make(sb, kind, N, seed):
+    if kind == "tri":
+        d = synth.random_tri_diagonals(seed=seed, N=N)
+        a, b, c = d
+        bh, ch = banded.tri_factor(a, b, c)
+        return sb.sb_factor_shared_tri(*d), (lambda r: banded.tri_solve(a, bh, ch, r))
+    d = synth.random_penta_diagonals(seed=seed, N=N)
+    fac = banded.penta_factor(*d)
+    return sb.sb_factor_shared_penta(*d), (lambda r: banded.penta_solve(*fac, r))
+
+
+@pytest.mark.parametrize("residual", ["native", "df32"])
+@pytest.mark.parametrize("kind", ["tri", "penta"])
+@pytest.mark.parametrize("N,M,ld", [(1, 5, 5), (2, 40, 41), (9, 100, 128), (300, 333, 333)])
+def test_refinement_contracts_to_fp64_accuracy(env, kind, N, M, ld, residual):
+    sb, torch = env
+    fac, ref_fn = make(sb, kind, N, seed=N + 3)
+    b32 = synth.rhs_uniform(seed=N, N=N, M=M, ld=ld, dtype=np.float32, pad_value=9.0)
+    ref = ref_fn(b32[:, :M].astype(np.float64))
+    d_b = to_dev(b32, torch)
+    work = torch.full((N, ld), -1.0, dtype=torch.float32, device="cuda")
+    errs = []
+    for n in (0, 1, 2):
+        x = torch.full((N, ld), 7.0, dtype=torch.float64, device="cuda")
+        sb.sb_solve_batched_refined(fac, d_b, x, n_refine=n, residual_arith=residual, work=work, M=M)
+        torch.cuda.synchronize()
+        out = to_host(x)
+        assert np.all(out[:, M:] == 7.0)
+        errs.append(np.max(relerr_per_system(out[:, :M], ref)))
+    assert errs[0] <= 2e-5
+    assert errs[2] <= 1e-10, errs
+    assert errs[1] <= max(errs[0] * 1e-2, 1e-13) and errs[2] <= max(errs[1], 1e-13), errs
+
+
+@pytest.mark.parametrize("arith,rt,xt,tol", [("native", "f64", "f64", 1e-12), ("df32", "f64", "f64", 1e-12),
+                                             ("df32", "f32", "f64", 1e-12), ("native", "f32", "f32", 2e-5)])
+def test_groups_without_refinement(env, arith, rt, xt, tol):
+    sb, torch = env
+    tdt = {"f64": torch.float64, "f32": torch.float32}
+    Ns, Ms = (5, 64, 300), (1000, 77, 300)
+    facs, refs, rhs, xs, hosts = [], [], [], [], []
+    for g, (N, M) in enumerate(zip(Ns, Ms)):
+        fac, ref_fn = make(sb, "penta", N, seed=100 + g)
+        h = synth.rhs_normal(seed=g, N=N, M=M).astype(np.float32 if rt == "f32" else np.float64)
+        facs.append(fac)
+        refs.append(ref_fn(h.astype(np.float64)))
+        rhs.append(to_dev(h, torch))
+        xs.append(torch.zeros((N, M), dtype=tdt[xt], device="cuda"))
+    sb.sb_solve_batched_groups(facs, rhs, xs, arith=arith)
+    torch.cuda.synchronize()
+    for g in range(3):
+        assert np.max(relerr_per_system(to_host(xs[g]), refs[g])) <= tol, g
+
+
+def test_groups_reject_mixed_bandwidth(env):
+    sb, torch = env
+    f1, _ = make(sb, "tri", 8, 1)
+    f2, _ = make(sb, "penta", 8, 2)
+    r = [torch.zeros((8, 4), dtype=torch.float64, device="cuda") for _ in range(2)]
+    x = [torch.zeros((8, 4), dtype=torch.float64, device="cuda") for _ in range(2)]
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_solve_batched_groups([f1, f2], r, x)
+    assert ei.value.code == sb.SB_ERR_UNSUPPORTED
+
+
+def test_refinement_rejects_missing_workspace(env):
+    sb, torch = env
+    fac, _ = make(sb, "tri", 16, 1)
+    b = torch.zeros((16, 8), dtype=torch.float32, device="cuda")
+    x = torch.zeros((16, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(sb.SbError):
+        sb.sb_solve_batched_refined(fac, b, x, n_refine=1, work=None)
+    small = torch.zeros(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(sb.SbError):
+        sb.sb_solve_batched_refined(fac, b, x, n_refine=1, work=small)
+
+
+def test_multigroup_workload_two_refinements(env):
+    """Three tridiagonal groups, 2^21 FP32 right-hand sides split 4:2:1, two
+    refinement passes with the FP64 residual, all groups in one call."""
+    sb, torch = env
+    w = synth.WORKLOADS["multigroup_fp32"]
+    Ms = synth.group_split(w["total"], w["ratio"], w["N"])
+    facs, rhs, xs, work = [], [], [], []
+    for g, (N, r, M) in enumerate(zip(w["N"], w["r"], Ms)):
+        facs.append(sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", N, r)))
+        rhs.append(synth.torch_uniform(w["seed"] + g, N, M, -1.0, 1.0, torch.float32, "cuda"))
+        xs.append(torch.empty((N, M), dtype=torch.float64, device="cuda"))
+        work.append(torch.empty((N, M), dtype=torch.float32, device="cuda"))
+    sb.sb_solve_batched_groups(facs, rhs, xs, n_refine=w["n_refine"], work=work)
+    torch.cuda.synchronize()
+    for g, (N, r, M) in enumerate(zip(w["N"], w["r"], Ms)):
+        cols = torch.as_tensor(np.linspace(0, M - 1, 256).astype(np.int64), device="cuda")
+        b = to_host(rhs[g][:, cols]).astype(np.float64)
+        A = steppers.SharedTri(*matrices.diffusion_matrix(N, r))
+        err = relerr_per_system(to_host(xs[g][:, cols]), A.solve(b))
+        assert np.max(err) <= 1e-10, (g, np.max(err))
