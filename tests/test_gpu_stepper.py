@@ -57,6 +57,7 @@ def test_stepper_matches_oracle(env, kind, scheme, bc, coef, dt, amp, N, arith, 
     d = to_dev(C0, torch)
     work = torch.empty_like(d) if mode == "unfused" else None
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())  # the copy to `d` ran on the default stream
     with torch.cuda.stream(stream):
         sb.sb_stepper_run(st, d, nsteps, arith=arith, mode=mode, work=work, M=M, stream=stream)
     torch.cuda.synchronize()
@@ -100,6 +101,7 @@ def _ch_workload(sb, torch, arith, nsteps):
     mass0 = C0.sum(dim=0)
     C = C0.clone()
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())  # C was produced on the default stream
     with torch.cuda.stream(stream):
         sb.sb_stepper_run(st, C, nsteps, arith=arith, mode="graph", stream=stream)
     torch.cuda.synchronize()
