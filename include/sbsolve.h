@@ -221,6 +221,27 @@ int sb_solve_batched_refined(const sb_factor* f, const float* rhs, double* x, in
                              size_t work_bytes, void* stream);
 
 /*
+ * sb_solve_batched_refined_noalloc -- sb_solve_batched_refined for callers that
+ * cannot allocate device memory when they solve (code inside a framework whose
+ * memory pool owns all allocations, allocation-free real-time loops, C callers
+ * without an allocator).  It takes no workspace and allocates nothing: its FP32
+ * scratch is a 16 MiB array compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.  The paper has no
+ * counterpart; this is a convenience of this library.
+ *
+ *   Limit: (N - 1) * ld + M <= 4194304 elements (4 Mi FP32 values), otherwise
+ *          SB_ERR_INVALID_ARG with a message; other arguments and results as for
+ *          sb_solve_batched_refined.
+ *   The first call on each device looks up the scratch array's device address
+ *   (and sets up the kernels); make that first call before any stream capture.
+ *   All calls share the one scratch array: calls that overlap on the GPU (other
+ *   streams, other host threads) race on it and must be serialised by the caller.
+ */
+int sb_solve_batched_refined_noalloc(const sb_factor* f, const float* rhs, double* x, int64_t M,
+                                     int64_t ld, int n_refine, sb_arith residual_arith,
+                                     void* stream);
+
+/*
  * sb_solve_batched_groups -- solve G (1..8) independent shared-LHS groups, each
  * with its own factor (its own N) and batch, with one kernel launch per pass:
  * the persistent CTAs are divided between the groups in proportion to N*M and

@@ -19,4 +19,5 @@ from ._lib import (  # noqa: F401
     sb_solve_batched_adjoint, sb_solve_batched_ex, sb_version, SB_ARITH_NATIVE, SB_ARITH_DF32,
     Shape, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run,
     sb_refine_workspace_bytes, sb_solve_batched_refined, sb_solve_batched_groups,
+    sb_solve_batched_refined_noalloc,
 )

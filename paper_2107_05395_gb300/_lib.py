@@ -74,6 +74,8 @@ SIGNATURES = {
     "sb_refine_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "sb_solve_batched_refined": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int,
                                                 _vp, ctypes.c_size_t, _vp]),
+    "sb_solve_batched_refined_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int,
+                                                        ctypes.c_int, _vp]),
     "sb_solve_batched_groups": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                _vp, _vp, _vp]),
@@ -303,6 +305,18 @@ def sb_solve_batched_refined(f: Factor, rhs, x, n_refine=2, residual_arith="nati
                                           _arith_code(residual_arith),
                                           None if work is None else _dev_ptr(work), _nbytes(work),
                                           _stream_handle(stream)))
+    return x
+
+
+def sb_solve_batched_refined_noalloc(f: Factor, rhs, x, n_refine=2, residual_arith="native",
+                                     M=None, ld=None, stream=None):
+    """Refined solve that allocates nothing: the FP32 scratch is the library's own
+    16 MiB device array, so (N-1)*ld + M must not exceed 4194304.  Calls that run
+    concurrently on the GPU share that array and must not overlap."""
+    M, ld = _batch_shape(rhs, f.N, M, ld)
+    _check(lib().sb_solve_batched_refined_noalloc(f.handle, _dev_ptr(rhs), _dev_ptr(x), M, ld,
+                                                  int(n_refine), _arith_code(residual_arith),
+                                                  _stream_handle(stream)))
     return x
 
 

@@ -481,3 +481,135 @@ int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Refined solve without any allocation by the caller.
+//
+// Some callers cannot allocate device memory at the point where they solve: code
+// running inside a framework whose memory pool owns every allocation, real-time
+// loops that must not call into the allocator, or plain C callers with no
+// allocator of their own.  For them sb_solve_batched_refined_noalloc takes its
+// FP32 scratch from the array below instead of a caller workspace.  The array is
+// a file-scope device variable, so every GPU that loads this library holds it
+// (16 MiB) until the process exits.  Every call uses the same array: calls that
+// overlap on the GPU (different streams, or different host threads) race on it.
+// The refinement pass writes each scratch element before reading it, so nothing
+// needs clearing between calls.
+namespace sb {
+namespace {
+
+constexpr size_t kNoAllocScratchElems = (size_t)4 << 20;  // 4 Mi FP32 values = 16 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device `dev` (looked up
+// once per device; the host symbol itself is not a device address).
+int noalloc_scratch(int dev, float** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(SB_ERR_UNSUPPORTED, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    SB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SB_OK;
+}
+
+// One launch of kernel k over a single group, sized from the occupancy query
+// (no caches, so no host containers grow).
+template <typename K, typename GA>
+int launch_one_group(K k, GA& a, int64_t N, int64_t M, size_t smem, int device,
+                     cudaStream_t stream) {
+  SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem));
+  if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "kernel cannot be resident (%zu B smem)", smem);
+  const int64_t need = (a.ntiles[0] + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nb * sm_count(device)));
+  a.G = 1;
+  a.cta_begin[0] = 0;
+  a.cta_begin[1] = grid;
+  (void)N;
+  (void)M;
+  k<<<grid, kThreads, smem, stream>>>(a);
+  return cuda_check(cudaGetLastError(), "kernel launch");
+}
+
+template <int P>
+int noalloc_refined(const sb_factor* f, const float* rhs, double* x, int64_t M, int64_t ld,
+                    int n_refine, sb_arith res, float* scratch, cudaStream_t stream) {
+  const int N = (int)f->N;
+  // first pass: FP32 sweeps of the FP32 right-hand side into the FP64 solution
+  {
+    Groups<float, float, double> a{};
+    a.coef[0] = f->coef32;
+    a.N[0] = N;
+    a.M[0] = M;
+    a.ld[0] = ld;
+    a.ntiles[0] = (M + 31) / 32;
+    a.rhs[0] = rhs;
+    a.x[0] = x;
+    const size_t smem = (size_t)2 * (P + 1) * N * sizeof(float);
+    SB_TRY(launch_one_group(grouped_sweep_kernel<NativeArith<float>, P, false, true, float, double>,
+                            a, N, M, smem, f->device, stream));
+  }
+  for (int k = 0; k < n_refine; ++k) {
+    Groups<float, float, double> a{};
+    a.coef[0] = f->coef32;
+    a.arow[0] = res == SB_ARITH_DF32 ? static_cast<const void*>(f->arowdf)
+                                     : static_cast<const void*>(f->arow64);
+    a.N[0] = N;
+    a.M[0] = M;
+    a.ld[0] = ld;
+    a.ntiles[0] = (M + 31) / 32;
+    a.rhs[0] = rhs;
+    a.x[0] = x;
+    a.work[0] = scratch;
+    const size_t smem = (size_t)(2 * P + 1) * N * 8 + (size_t)2 * (P + 1) * N * sizeof(float);
+    if (res == SB_ARITH_DF32)
+      SB_TRY(launch_one_group(grouped_refine_kernel<P, true>, a, N, M, smem, f->device, stream));
+    else
+      SB_TRY(launch_one_group(grouped_refine_kernel<P, false>, a, N, M, smem, f->device, stream));
+  }
+  return SB_OK;
+}
+
+}  // namespace
+}  // namespace sb
+
+extern "C" int sb_solve_batched_refined_noalloc(const sb_factor* f, const float* rhs, double* x,
+                                                int64_t M, int64_t ld, int n_refine,
+                                                sb_arith residual_arith, void* stream) {
+  clear_error();
+  if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  if (M < 0 || ld < M || ld < 1)
+    return fail(SB_ERR_INVALID_ARG, "need M >= 0 and ld >= max(M, 1)");
+  if (n_refine < 0 || n_refine > 16) return fail(SB_ERR_INVALID_ARG, "n_refine must be in [0, 16]");
+  if (residual_arith != SB_ARITH_NATIVE && residual_arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown residual arithmetic mode");
+  if (M == 0) return SB_OK;
+  if (ld > ((int64_t)1 << 40) / f->N) return fail(SB_ERR_INVALID_ARG, "N*ld too large");
+  const size_t elems = (size_t)((f->N - 1) * ld + M);
+  if (elems > kNoAllocScratchElems)
+    return fail(SB_ERR_INVALID_ARG,
+                "(N-1)*ld + M = %zu elements exceeds the allocation-free scratch of %zu elements "
+                "(16 MiB); use sb_solve_batched_refined with a workspace instead",
+                elems, kNoAllocScratchElems);
+  const size_t smem = (size_t)(2 * f->P + 1) * f->N * 8 + (size_t)2 * (f->P + 1) * f->N * 4;
+  if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "N too large for shared memory");
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  SB_TRY(check_device_range(rhs, elems * sizeof(float), sizeof(float), f->device, "rhs"));
+  SB_TRY(check_device_range(x, elems * sizeof(double), sizeof(double), f->device, "x"));
+  SB_TRY(check_alias(rhs, elems * sizeof(float), x, elems * sizeof(double), "rhs", "x"));
+  if ((const void*)rhs == (const void*)x) return fail(SB_ERR_INVALID_ARG, "x must not alias rhs");
+  float* scratch = nullptr;
+  SB_TRY(noalloc_scratch(f->device, &scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  return f->P == 1 ? noalloc_refined<1>(f, rhs, x, M, ld, n_refine, residual_arith, scratch, s)
+                   : noalloc_refined<2>(f, rhs, x, M, ld, n_refine, residual_arith, scratch, s);
+}
