@@ -6,6 +6,7 @@ The paper has no counterpart for this part (it only runs rollouts forward).  The
 rollout is x_{n+1} = A(p)^{-1} F(x_n), n = 0 .. T-1, with
 
 * diffusion:       A = I + r K (Dirichlet), F = identity, parameter p = r;
+* hyperdiffusion:  A = I + r D4 (hinged closure), F = identity, parameter p = r;
 * Cahn-Hilliard:   A = I + dt gamma D4_N, F(x) = x + dt D2_N (x^3 - x),
                    parameter p = gamma (in grid units, dt fixed).
 
@@ -19,7 +20,7 @@ every state (no checkpointing) and runs the textbook reverse sweep:
         gbar_n  = J_F(x_n)^T mu
     dL/dx_0 = gbar_0
 
-with dA/dr = K, dA/dgamma = dt D4_N, and J_F(x)^T mu = mu + dt (3 x^2 - 1) * (D2_N^T mu).
+with dA/dr = K (diffusion) or D4 (hyperdiffusion), dA/dgamma = dt D4_N, and J_F(x)^T mu = mu + dt (3 x^2 - 1) * (D2_N^T mu).
 Systems never interact, so any subset of columns can be run on its own; the
 parameter gradient is then the sum of the per-system contributions returned here.
 """
@@ -29,7 +30,7 @@ import numpy as np
 
 from . import matrices, steppers
 
-__all__ = ["Problem", "diffusion_problem", "ch_problem", "forward", "loss", "adjoint"]
+__all__ = ["Problem", "diffusion_problem", "hyperdiffusion_problem", "ch_problem", "forward", "loss", "adjoint"]
 
 
 class Problem:
@@ -41,6 +42,9 @@ class Problem:
             self.A = steppers.SharedTri(*matrices.diffusion_matrix(N, self.param))
             sub, dia, sup = matrices.d2_dirichlet(N)
             self.dA = (-sub, -dia, -sup)                     # K = -D2_D
+        elif kind == "hyperdiffusion":
+            self.A = steppers.SharedPenta(*matrices.hyperdiffusion_matrix(N, self.param, "hinged"))
+            self.dA = matrices.square_tridiag(*matrices.d2_dirichlet(N))   # D4 (hinged)
         elif kind == "cahn_hilliard":
             self.A = steppers.SharedPenta(*matrices.ch_matrix(N, dt * self.param))
             self.dA = tuple(dt * v for v in matrices.square_tridiag(*matrices.d2_noflux(N)))
@@ -49,13 +53,13 @@ class Problem:
             raise ValueError(kind)
 
     def F(self, x):
-        if self.kind == "diffusion":
+        if self.kind in ("diffusion", "hyperdiffusion"):
             return np.asarray(x, dtype=np.float64).copy()
         return steppers.ch_rhs(x, self.dt)
 
     def F_adjoint(self, x, mu):
         """J_F(x)^T mu."""
-        if self.kind == "diffusion":
+        if self.kind in ("diffusion", "hyperdiffusion"):
             return mu.copy()
         sub, dia, sup = self.d2n
         # transpose of a tridiagonal matrix: sub-diagonal of T^T is super of T shifted
@@ -69,11 +73,17 @@ class Problem:
     def apply_dA(self, x):
         if self.kind == "diffusion":
             return matrices.apply_tri(*self.dA, x)
+        if self.kind == "hyperdiffusion":
+            return matrices.apply_penta(*self.dA, x)
         return matrices.apply_penta(*self.dA, x)
 
 
 def diffusion_problem(N, r):
     return Problem("diffusion", N, r)
+
+
+def hyperdiffusion_problem(N, r):
+    return Problem("hyperdiffusion", N, r)
 
 
 def ch_problem(N, gamma, dt):

@@ -23,6 +23,13 @@ def make_case(kind):
         y = synth.rhs_uniform(seed=51, N=N, M=M)
         builder = lambda p: rollout.diffusion_problem(N, p)
         p0 = 0.5
+    elif kind == "hyperdiffusion":
+        N, M, T = 14, 3, 6
+        prob = rollout.hyperdiffusion_problem(N, 0.25)
+        x0 = synth.rhs_uniform(seed=56, N=N, M=M)
+        y = synth.rhs_uniform(seed=57, N=N, M=M)
+        builder = lambda p: rollout.hyperdiffusion_problem(N, p)
+        p0 = 0.25
     elif kind == "ch_grid":
         N, M, T = 16, 3, 6
         prob = rollout.ch_problem(N, synth.CH_GAMMA_GRID, synth.CH_DT_GRID)
@@ -40,7 +47,7 @@ def make_case(kind):
     return prob, x0, y, T, builder, p0
 
 
-@pytest.mark.parametrize("kind", ["diffusion", "ch_grid", "ch_nonlinear"])
+@pytest.mark.parametrize("kind", ["diffusion", "hyperdiffusion", "ch_grid", "ch_nonlinear"])
 def test_adjoint_initial_condition_vs_fd(kind):
     prob, x0, y, T, _, _ = make_case(kind)
     L, gx0, _ = rollout.adjoint(prob, x0, y, T)
@@ -52,7 +59,7 @@ def test_adjoint_initial_condition_vs_fd(kind):
         assert abs(ad - fd) <= 1e-8 * max(abs(fd), 1e-12) + 1e-14
 
 
-@pytest.mark.parametrize("kind", ["diffusion", "ch_grid", "ch_nonlinear"])
+@pytest.mark.parametrize("kind", ["diffusion", "hyperdiffusion", "ch_grid", "ch_nonlinear"])
 def test_adjoint_parameter_vs_fd(kind):
     prob, x0, y, T, builder, p0 = make_case(kind)
     _, _, dp = rollout.adjoint(prob, x0, y, T)
