@@ -313,6 +313,41 @@ int sb_stepper_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size
 int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
                    int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream);
 
+/*
+ * Differentiable rollouts (S8 + S9 of the hot path; no counterpart in the paper,
+ * which only runs forward).  For a backward-Euler diffusion / hyperdiffusion or a
+ * Cahn-Hilliard stepper, the rollout x_{n+1} = A(p)^{-1} F(x_n), n < nsteps, with p
+ * the stepper's coefficient (r, or gamma), and a loss L(x_T) chosen by the caller:
+ *
+ *   sb_rollout_forward   x_T from x_0 = C0, keeping a checkpoint every ckpt_every
+ *                        steps in `work`.
+ *   sb_rollout_backward  from grad_CT = dL/dx_T: grad_C0 = dL/dx_0, and dL/dp per
+ *                        system (M doubles, optional) and summed over the batch
+ *                        (one double, optional; a fixed-order sum, so repeatable).
+ *                        Recomputes each segment from its checkpoint (bitwise the
+ *                        forward states), then per step one fused kernel:
+ *                        mu = A^{-T} gbar (same factors), dL/dp -= mu.(dA/dp)x_{n+1},
+ *                        gbar <- J_F(x_n)^T mu.  The adjoint arithmetic is FP64;
+ *                        `arith` selects the arithmetic of the recomputed steps and
+ *                        must match the forward call.
+ *
+ * All arrays are device FP64 in the N x ld interleaved layout (grad outputs must
+ * not overlap `work`).  `work` is caller-owned, sb_rollout_workspace_bytes() bytes:
+ * (ceil(nsteps/ckpt_every) + ckpt_every + 2) states of N*ld doubles plus M + 256
+ * doubles.  The same work buffer (unchanged between the calls), sizes, nsteps,
+ * ckpt_every and arith must be passed to the forward and backward calls.
+ * Crank-Nicolson steppers return SB_ERR_UNSUPPORTED.
+ */
+int sb_rollout_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, int64_t nsteps,
+                               int64_t ckpt_every, size_t* bytes);
+int sb_rollout_forward(sb_stepper* st, const double* C0, double* CT, int64_t M, int64_t ld,
+                       int64_t nsteps, int64_t ckpt_every, sb_arith arith, void* work,
+                       size_t work_bytes, void* stream);
+int sb_rollout_backward(sb_stepper* st, const double* grad_CT, double* grad_C0,
+                        double* grad_param_per_system, double* grad_param, int64_t M, int64_t ld,
+                        int64_t nsteps, int64_t ckpt_every, sb_arith arith, void* work,
+                        size_t work_bytes, void* stream);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char* sb_last_error(void);
 

@@ -11,6 +11,7 @@ CUDA kernels behind the C ABI in ``include/sbsolve.h``.
 This package is the Python side of that ABI: ctypes marshalling only.  Build the
 library with ``python -m paper_2107_05395_gb300.build``.
 """
+from .autograd import SharedLHSRollout  # noqa: F401,E402
 from ._lib import (  # noqa: F401
     SB_ERR_ALLOC, SB_ERR_CUDA, SB_ERR_INVALID_ARG, SB_ERR_SINGULAR, SB_ERR_UNSUPPORTED,
     SB_F32, SB_F64, SB_OK, SIGNATURES, MATRIX_KINDS, Factor, SbError, lib, sb_build_matrix,
@@ -19,5 +20,6 @@ from ._lib import (  # noqa: F401
     sb_solve_batched_adjoint, sb_solve_batched_ex, sb_version, SB_ARITH_NATIVE, SB_ARITH_DF32,
     Shape, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run,
     sb_refine_workspace_bytes, sb_solve_batched_refined, sb_solve_batched_groups,
-    sb_solve_batched_refined_noalloc,
+    sb_solve_batched_refined_noalloc, sb_rollout_workspace_bytes, sb_rollout_forward,
+    sb_rollout_backward,
 )

@@ -79,6 +79,12 @@ SIGNATURES = {
     "sb_solve_batched_groups": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                _vp, _vp, _vp]),
+    "sb_rollout_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64,
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "sb_rollout_forward": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, ctypes.c_int,
+                                          _vp, ctypes.c_size_t, _vp]),
+    "sb_rollout_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64,
+                                           ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "sb_stepper_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i64, ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(_vp)]),
     "sb_stepper_destroy": (None, [_vp]),
@@ -392,6 +398,33 @@ def sb_stepper_run(st: Stepper, state, nsteps, arith="native", mode="graph", wor
                                 RUN_MODES[mode] if isinstance(mode, str) else int(mode), wptr or None,
                                 wbytes, _stream_handle(stream)))
     return state
+
+
+def sb_rollout_workspace_bytes(st: Stepper, M, nsteps, ckpt_every, ld=None):
+    out = ctypes.c_size_t()
+    _check(lib().sb_rollout_workspace_bytes(st.handle, M, M if ld is None else ld, int(nsteps),
+                                            int(ckpt_every), ctypes.byref(out)))
+    return out.value
+
+
+def sb_rollout_forward(st: Stepper, C0, CT, nsteps, ckpt_every, work, arith="native", M=None, ld=None,
+                       stream=None):
+    M, ld = _batch_shape(C0, st.N, M, ld)
+    _check(lib().sb_rollout_forward(st.handle, _dev_ptr(C0), _dev_ptr(CT), M, ld, int(nsteps),
+                                    int(ckpt_every), _arith_code(arith), _dev_ptr(work), _nbytes(work),
+                                    _stream_handle(stream)))
+    return CT
+
+
+def sb_rollout_backward(st: Stepper, grad_CT, grad_C0, nsteps, ckpt_every, work, grad_param=None,
+                        grad_param_per_system=None, arith="native", M=None, ld=None, stream=None):
+    M, ld = _batch_shape(grad_CT, st.N, M, ld)
+    _check(lib().sb_rollout_backward(
+        st.handle, _dev_ptr(grad_CT), _dev_ptr(grad_C0),
+        None if grad_param_per_system is None else _dev_ptr(grad_param_per_system),
+        None if grad_param is None else _dev_ptr(grad_param), M, ld, int(nsteps), int(ckpt_every),
+        _arith_code(arith), _dev_ptr(work), _nbytes(work), _stream_handle(stream)))
+    return grad_C0
 
 
 def sb_last_error() -> str:

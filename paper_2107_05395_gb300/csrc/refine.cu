@@ -244,7 +244,7 @@ int resident_ctas(K kernel, int device, size_t smem, int* total) {
     if (it != cache.end()) {
       nb = it->second;
     } else {
-      SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
       SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem));
       cache[key] = nb;
     }
@@ -524,7 +524,7 @@ int noalloc_scratch(int dev, float** out) {
 template <typename K, typename GA>
 int launch_one_group(K k, GA& a, int64_t N, int64_t M, size_t smem, int device,
                      cudaStream_t stream) {
-  SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
   int nb = 0;
   SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem));
   if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "kernel cannot be resident (%zu B smem)", smem);

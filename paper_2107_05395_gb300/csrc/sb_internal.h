@@ -3,7 +3,10 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -45,6 +48,11 @@ int cuda_check(cudaError_t e, const char* what);
 // One "op" block = [forward rows 0..N-1][backward rows 0..N-1].
 inline int64_t op_block_len(int P, int64_t N) { return 2 * (P + 1) * N; }
 
+// Every kernel's dynamic shared-memory limit is raised once to the opt-in maximum
+// of a GB300 CTA (227 KB), never to the size of one launch: a limit lowered for a
+// small-N launch would make a later, larger launch of the same kernel fail.
+constexpr int kMaxDynSmem = 227 * 1024;
+
 enum Op { OP_PRIMAL = 0, OP_ADJOINT = 1 };
 
 // Launch shape of the sweep kernel (chosen by default_shape or the autotuner).
@@ -68,6 +76,21 @@ struct sb_factor {
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64
+};
+
+struct sb_stepper {
+  // stepper.cu: scheme, factor of A and right-hand-side rows; rollout.cu: dA rows
+  int kind = 0, scheme = 0, bc = 0;
+  int64_t N = 0;
+  double coef = 0.0, dt = 0.0;
+  sb_factor* fac = nullptr;
+  int NB = 0;            // B band width (0 = identity)
+  bool has_e = false;
+  double* r64 = nullptr;  // device rhs coefficient rows, FP64
+  float* rdf = nullptr;   // same as (hi, lo) pairs
+  double* dA64 = nullptr;  // d A / d coef row by row ((2P+1) per row), for the rollout adjoint
+  std::mutex mu;
+  std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
 };
 
 namespace sb {
@@ -97,6 +120,9 @@ int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, i
 SweepShape default_shape(const sb_factor* f, sb_arith arith);
 // Tuned shape for (device, P, N, arith, dtypes) or the default (tune.cpp).
 SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype xt);
+// One fused stepper step from src into dst (stepper.cu).
+int stepper_step(const sb_stepper* st, const double* src, double* dst, int64_t M, int64_t ld,
+                 sb_arith arith, cudaStream_t stream);
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream);

@@ -43,7 +43,7 @@ struct StConv<DFArith, double> {
 template <class A, int P, int NB, bool HAS_E, int R>
 __global__ void __launch_bounds__(512)
 fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
-                  int N, int64_t M, int64_t ld, double* state, int64_t ntiles) {
+                  int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles) {
   using V = typename A::V;
   using C = typename A::C;
   using S = typename A::S;
@@ -69,7 +69,8 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
        tile += (int64_t)gridDim.x * nw) {
     const int64_t m = tile * 32 + lane;
     if (m >= M) continue;
-    double* y = state + m;
+    double* y = state + m;     // intermediates and the new state
+    const double* c = src + m;  // the old state (may be the same array as y)
 
     // window: cw[k] = C_{i-2+k}, pw[k] = phi(C_{i-1+k}) for the row i being built
     V cw[5], pw[3];
@@ -81,7 +82,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     auto load_rows = [&](double (&buf)[R], int i0) {
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        if (i0 + j < N) buf[j] = y[(int64_t)(i0 + j) * ld];
+        if (i0 + j < N) buf[j] = c[(int64_t)(i0 + j) * ld];
     };
     // push raw row k (value v, already 0 when k >= N) into the windows
     auto push = [&](double v) {
@@ -211,18 +212,7 @@ __global__ void rhs_kernel(const typename A::C* __restrict__ rcoef, int N, int64
 
 // ------------------------------------------------------------------ host side
 
-struct sb_stepper {
-  int kind = 0, scheme = 0, bc = 0;
-  int64_t N = 0;
-  double coef = 0.0, dt = 0.0;
-  sb_factor* fac = nullptr;
-  int NB = 0;            // B band width (0 = identity)
-  bool has_e = false;
-  double* r64 = nullptr;  // device rhs coefficient rows, FP64
-  float* rdf = nullptr;   // same as (hi, lo) pairs
-  std::mutex mu;
-  std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
-};
+
 
 namespace sb {
 namespace {
@@ -232,7 +222,7 @@ constexpr int kGraphSteps = 64;  // steps per captured graph
 
 template <class A, int P, int NB, bool HAS_E>
 int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
-                 double* state, int64_t M, int64_t ld, cudaStream_t stream) {
+                 const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const sb_factor* f = st->fac;
   const int N = (int)f->N;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
@@ -249,7 +239,7 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
     auto key = std::make_pair(reinterpret_cast<const void*>(k), (int)smem);
     auto it = occ.find(key);
     if (it == occ.end()) {
-      SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
       SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem));
       occ[key] = nb;
     } else {
@@ -260,7 +250,7 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
   const int64_t ntiles = (M + 31) / 32;
   const int64_t want = (ntiles + threads / 32 - 1) / (threads / 32);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(f->device)));
-  k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, state, ntiles);
+  k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles);
   return cuda_check(cudaGetLastError(), "fused step launch");
 }
 
@@ -275,14 +265,14 @@ int launch_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, 
 
 template <class A>
 int one_step(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
-             double* state, int64_t M, int64_t ld, cudaStream_t stream) {
+             const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const int P = st->fac->P;
-  if (st->has_e) return launch_fused<A, 2, 0, true>(st, coef, rc, state, M, ld, stream);
+  if (st->has_e) return launch_fused<A, 2, 0, true>(st, coef, rc, src, state, M, ld, stream);
   if (P == 1)
-    return st->NB == 3 ? launch_fused<A, 1, 3, false>(st, coef, rc, state, M, ld, stream)
-                       : launch_fused<A, 1, 0, false>(st, coef, rc, state, M, ld, stream);
-  return st->NB == 5 ? launch_fused<A, 2, 5, false>(st, coef, rc, state, M, ld, stream)
-                     : launch_fused<A, 2, 0, false>(st, coef, rc, state, M, ld, stream);
+    return st->NB == 3 ? launch_fused<A, 1, 3, false>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false>(st, coef, rc, src, state, M, ld, stream);
+  return st->NB == 5 ? launch_fused<A, 2, 5, false>(st, coef, rc, src, state, M, ld, stream)
+                     : launch_fused<A, 2, 0, false>(st, coef, rc, src, state, M, ld, stream);
 }
 
 template <class A>
@@ -294,14 +284,22 @@ int one_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, dou
   return launch_rhs<A, 0, false>(st, rc, in, out, M, ld, stream);
 }
 
-int step_fused(const sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
-               cudaStream_t stream) {
+}  // namespace
+
+// One fused step from `src` into `dst` (the same array for an in-place step).
+int stepper_step(const sb_stepper* st, const double* src, double* dst, int64_t M, int64_t ld,
+                 sb_arith arith, cudaStream_t stream) {
   if (arith == SB_ARITH_DF32)
     return one_step<DFArith>(st, reinterpret_cast<const df*>(st->fac->coefdf),
-                             reinterpret_cast<const df*>(st->rdf), state, M, ld, stream);
-  return one_step<NativeArith<double>>(st, st->fac->coef64, st->r64, state, M, ld, stream);
+                             reinterpret_cast<const df*>(st->rdf), src, dst, M, ld, stream);
+  return one_step<NativeArith<double>>(st, st->fac->coef64, st->r64, src, dst, M, ld, stream);
 }
 
+namespace {
+int step_fused(const sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+               cudaStream_t stream) {
+  return stepper_step(st, state, state, M, ld, arith, stream);
+}
 }  // namespace
 }  // namespace sb
 

@@ -60,7 +60,7 @@ int prepare(K kernel, int device, int threads, size_t smem, int* blocks_per_sm) 
       return SB_OK;
     }
   }
-  SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
   int nb = 0;
   SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
   if (nb < 1)
