@@ -220,6 +220,141 @@ def profiled_traffic():
     return float(t.group(1))
 
 
+# ------------------------------------------------------- the other workloads
+
+def _events_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_tri_latency(sb, torch, stream):
+    """Tridiagonal backward-Euler solve, N=256, M=1024 (4 MiB): latency per solve
+    from a CUDA graph of 100 solves (native FP64 and double-float)."""
+    import synth
+    w = synth.WORKLOADS["tri_dirichlet"]
+    N, M = w["N"], w["M"]
+    fac = sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", N, w["r"]))
+    rhs = synth.torch_uniform(w["seed"], N, M, -1.0, 1.0, torch.float64, "cuda")
+    x = torch.empty_like(rhs)
+    out = {}
+    for arith in ("native", "df32"):
+        sb.sb_autotune(fac, rhs, x, arith=arith)
+        sb.sb_solve_batched_ex(fac, rhs, x, arith=arith)  # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            for _ in range(100):
+                sb.sb_solve_batched_ex(fac, rhs, x, arith=arith)
+        g.replay()
+        ms = _events_ms(g.replay, 5, torch.cuda.current_stream()) / 100
+        out[arith] = {"us_per_solve": ms * 1e3, "solves_per_s": 1e3 / ms}
+    return {"workload": "tri N=256, M=1024, r=0.5, U[-1,1]", **out}
+
+
+def extra_multigroup(sb, torch, stream):
+    """Three tridiagonal groups (N=128/512/2048, r=0.1/0.5/2.0), 2^21 FP32 RHS split
+    4:2:1, FP64 solutions: two refinements (FP64 and double-float residual) against
+    a single double-float pass, all groups per launch.  Error: max relative L2 on
+    256 systems per group against the native FP64 solve of the promoted RHS."""
+    import synth
+    w = synth.WORKLOADS["multigroup_fp32"]
+    Ms = synth.group_split(w["total"], w["ratio"], w["N"])
+    facs, rhs, xs, work, ref = [], [], [], [], []
+    for g, (N, r, M) in enumerate(zip(w["N"], w["r"], Ms)):
+        facs.append(sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", N, r)))
+        rhs.append(synth.torch_uniform(w["seed"] + g, N, M, -1.0, 1.0, torch.float32, "cuda"))
+        xs.append(torch.empty((N, M), dtype=torch.float64, device="cuda"))
+        work.append(torch.empty((N, M), dtype=torch.float32, device="cuda"))
+        cols = torch.as_tensor([int(v) for v in __import__("numpy").linspace(0, M - 1, 256)], device="cuda")
+        b64 = rhs[-1][:, cols].double().contiguous()
+        xr = torch.empty_like(b64)
+        sb.sb_solve_batched(facs[-1], b64, xr)
+        ref.append((cols, xr))
+    elts = sum(N * M for N, M in zip(w["N"], Ms))
+
+    def err():
+        worst = []
+        for g in range(3):
+            cols, xr = ref[g]
+            d = xs[g][:, cols] - xr
+            worst.append(float((d.norm(dim=0) / xr.norm(dim=0)).max().item()))
+        return worst
+
+    out = {"workload": "3 tri groups N=128/512/2048, 2^21 FP32 RHS 4:2:1 -> FP64",
+           "elements": elts}
+    variants = [("refine2_fp64_residual", dict(arith="native", n_refine=2, residual_arith="native")),
+                ("refine2_df32_residual", dict(arith="native", n_refine=2, residual_arith="df32")),
+                ("df32_direct", dict(arith="df32", n_refine=0)),
+                ("fp32_only", dict(arith="native", n_refine=0))]
+    for name, kw in variants:
+        fn = lambda: sb.sb_solve_batched_groups(facs, rhs, xs, work=work, **kw)
+        fn()
+        ms = _events_ms(fn, 3, torch.cuda.current_stream())
+        out[name] = {"ms_per_call": ms, "launches": 1 + kw.get("n_refine", 0),
+                     "algorithmic_gbs": 12.0 * elts / (ms * 1e-3) / 1e9, "max_rel_err_per_group": err()}
+    return out
+
+
+def extra_cahn_hilliard(sb, torch, stream):
+    """Cahn-Hilliard, N=256, 2^20 simulations: ms per step for the fused + graphed
+    step (FP64 and double-float) and the unfused two-kernel step (FP64)."""
+    import synth
+    w = synth.WORKLOADS["cahn_hilliard"]
+    N, M = w["N"], w["M"]
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "noflux", N, w["gamma"], w["dt"])
+    C = synth.torch_uniform(w["seed"], N, M, -w["amp"], w["amp"], torch.float64, "cuda")
+    work = torch.empty_like(C)
+    out = {"workload": "CH N=256, M=2^20, gamma'=16.6, dt'=1e-3 (64 steps timed)"}
+    for name, arith, mode in (("fused_graph_fp64", "native", "graph"), ("fused_graph_df32", "df32", "graph"),
+                              ("unfused_fp64", "native", "unfused"), ("unfused_df32", "df32", "unfused")):
+        sb.sb_stepper_run(st, C, 64, arith=arith, mode=mode, work=work)
+        ms = _events_ms(lambda: sb.sb_stepper_run(st, C, 64, arith=arith, mode=mode, work=work), 2,
+                        torch.cuda.current_stream()) / 64
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                     "algorithmic_gbs": 16.0 * N * M / (ms * 1e-3) / 1e9}
+    return out
+
+
+def extra_rollout(sb, torch, stream):
+    """Adjoint rollout, N=512, 2^16 systems, 200 steps, checkpoints every 20 (CH
+    and diffusion, FP64): forward and backward step rates against the plain
+    per-step solve of the same stepper."""
+    import synth
+    w = synth.WORKLOADS["adjoint_rollout"]
+    N, M, T, k = w["N"], w["M"], w["steps"], w["ckpt_every"]
+    out = {"workload": "rollout N=512, M=2^16, 200 steps, ckpt 20, FP64"}
+    for kind, p, dt, bc in (("cahn_hilliard", w["gamma"], w["dt"], "noflux"), ("diffusion", w["r"], 0.0, "dirichlet")):
+        st = sb.sb_stepper_create(kind, "be", bc, N, p, dt)
+        x0 = synth.torch_uniform(w["seed"], N, M, -0.1, 0.1, torch.float64, "cuda")
+        work = torch.empty(sb.sb_rollout_workspace_bytes(st, M, T, k) // 8, dtype=torch.float64, device="cuda")
+        CT = torch.empty_like(x0)
+        g = torch.empty_like(x0)
+        gC0 = torch.empty_like(x0)
+        dp = torch.zeros((), dtype=torch.float64, device="cuda")
+        fwd = lambda: sb.sb_rollout_forward(st, x0, CT, T, k, work)
+        bwd = lambda: sb.sb_rollout_backward(st, g, gC0, T, k, work, grad_param=dp)
+        fwd()
+        g.copy_(CT)
+        bwd()
+        f_ms = _events_ms(fwd, 1, torch.cuda.current_stream())
+        b_ms = _events_ms(bwd, 1, torch.cuda.current_stream())
+        C = x0.clone()
+        plain = _events_ms(lambda: sb.sb_stepper_run(st, C, 20, mode="direct"), 1,
+                           torch.cuda.current_stream()) / 20
+        out[kind] = {"forward_ms": f_ms, "backward_ms": b_ms,
+                     "forward_steps_per_s": T / (f_ms * 1e-3), "backward_steps_per_s": T / (b_ms * 1e-3),
+                     "plain_step_ms": plain, "backward_vs_plain_step": (b_ms / T) / plain}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -316,6 +451,16 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    extras = {}
+    if not args.no_extras:
+        for name, fn in (("tri_latency", extra_tri_latency), ("multigroup_refine", extra_multigroup),
+                         ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout)):
+            try:
+                extras[name] = fn(sb, torch, stream)
+            except Exception as exc:  # report, do not hide, a failing extra
+                extras[name] = {"error": repr(exc)}
+            torch.cuda.empty_cache()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -364,6 +509,7 @@ def run_ours(args):
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8},
         "extras": {
+            **extras,
             f"solve_{other}": {"shape": list(shapes[other][0]),
                                "ms_per_solve": float(np.mean(other_ms)),
                                "batched_solves_per_s": 1.0 / other_s,
@@ -388,6 +534,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arith", choices=["native", "df32"], default="native")
+    ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
