@@ -61,7 +61,7 @@ grouped_sweep_kernel(const __grid_constant__ Groups<typename A::C, TI, TO> a) {
   __syncthreads();
   const int nw = blockDim.x >> 5;
   const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
-  for (int64_t tile = (int64_t)(blockIdx.x - a.cta_begin[g]) * nw + (threadIdx.x >> 5);
+  for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
        tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
     sweep_tile<A, P, F_ONE, B_ONE, TI, TO, 1, kRows>(cs, cs + W * N, N, a.M[g], a.ld[g],
                                                      a.rhs[g], a.x[g], tile);
@@ -222,7 +222,7 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, float, double> a) {
   __syncthreads();
   const int nw = blockDim.x >> 5;
   const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
-  for (int64_t tile = (int64_t)(blockIdx.x - a.cta_begin[g]) * nw + (threadIdx.x >> 5);
+  for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
        tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
     refine_tile<P, DFRES, kRows>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g],
                                  a.work[g], tile);
@@ -263,7 +263,7 @@ int plan(GA& a, const std::vector<const sb_factor*>& f, int total) {
   for (int g = 0; g < a.G; ++g) work += (double)f[g]->N * (double)a.M[g];
   int begin = 0;
   for (int g = 0; g < a.G; ++g) {
-    const int64_t need = (a.ntiles[g] + nw - 1) / nw;
+    const int64_t need = a.ntiles[g];
     int64_t share = (int64_t)std::llround(total * ((double)f[g]->N * (double)a.M[g]) / work);
     share = std::max<int64_t>(1, std::min<int64_t>(share, need));
     a.cta_begin[g] = begin;
@@ -528,8 +528,7 @@ int launch_one_group(K k, GA& a, int64_t N, int64_t M, size_t smem, int device,
   int nb = 0;
   SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem));
   if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "kernel cannot be resident (%zu B smem)", smem);
-  const int64_t need = (a.ntiles[0] + kThreads / 32 - 1) / (kThreads / 32);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nb * sm_count(device)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntiles[0], (int64_t)nb * sm_count(device)));
   a.G = 1;
   a.cta_begin[0] = 0;
   a.cta_begin[1] = grid;

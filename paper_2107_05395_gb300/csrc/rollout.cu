@@ -53,7 +53,7 @@ adjoint_step_kernel(const double* __restrict__ coef, const double* __restrict__ 
   __syncthreads();
 
   const int nw = blockDim.x >> 5;
-  for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
        tile += (int64_t)gridDim.x * nw) {
     const int64_t m = tile * 32 + (threadIdx.x & 31);
     if (m >= M) continue;
@@ -274,8 +274,7 @@ int launch_adjoint(const sb_stepper* st, double* G, const double* Xn1, const dou
   }
   if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "adjoint kernel cannot be resident");
   const int64_t ntiles = (M + 31) / 32;
-  const int64_t want = (ntiles + kAdjThreads / 32 - 1) / (kAdjThreads / 32);
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(st->fac->device)));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(st->fac->device)));
   const double* coef = st->fac->coef64 + op_block_len(P, N);  // adjoint block
   k<<<(unsigned)grid, kAdjThreads, smem, s>>>(coef, st->dA64, st->r64, N, M, ld, G, Xn1, Xn, dp, ntiles);
   return cuda_check(cudaGetLastError(), "adjoint step launch");

@@ -65,7 +65,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
 
   const int lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
-  for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
        tile += (int64_t)gridDim.x * nw) {
     const int64_t m = tile * 32 + lane;
     if (m >= M) continue;
@@ -248,8 +248,7 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
   }
   if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "fused step kernel cannot be resident");
   const int64_t ntiles = (M + 31) / 32;
-  const int64_t want = (ntiles + threads / 32 - 1) / (threads / 32);
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(f->device)));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
   k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles);
   return cuda_check(cudaGetLastError(), "fused step launch");
 }

@@ -35,7 +35,7 @@ sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t l
   stage(cs, coef, 2 * W * N);
   __syncthreads();
   const int nw = blockDim.x >> 5;
-  for (int64_t tile = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); tile < ntiles;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
        tile += (int64_t)gridDim.x * nw)
     sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R>(cs, cs + W * N, N, M, ld, rhs, x, tile);
 }
@@ -88,9 +88,10 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   SB_TRY(prepare(k, f->device, threads, smem, &nb));
   if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
   const int64_t ntiles = (M + 32 * SPT - 1) / (32 * SPT);
-  const int64_t want = (ntiles + threads / 32 - 1) / (threads / 32);
+  // one CTA per resident slot at most, tiles dealt round-robin over the CTAs first
+  // (tile = block + grid * warp) so that every SM gets an equal share
   const int64_t grid =
-      std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nb * sm_count(f->device)));
+      std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
   k<<<(unsigned)grid, threads, smem, stream>>>(coef, N, M, ld, static_cast<const TI*>(rhs),
                                               static_cast<TO*>(x), ntiles);
   return cuda_check(cudaGetLastError(), "sweep kernel launch");
