@@ -21,6 +21,7 @@
 #include <mutex>
 #include <vector>
 
+#include "arith.cuh"
 #include "sb_internal.h"
 
 namespace sb {
@@ -129,7 +130,7 @@ adjoint_step_kernel(const double* __restrict__ coef, const double* __restrict__ 
           const int k = j + P;  // x_{n+1} row i - P
           push(i - P >= 0 ? (k < R ? y[k] : yn[k - R]) : 0.0);
           const double* c = bw + W * i;
-          double mu = c[0] * w[j];
+          double mu = dmul_int(c[0], w[j]);  // off the chain: integer pipe, bit-identical
           mu = fma(-c[1], mu1, mu);
           if constexpr (P == 2) mu = fma(-c[2], mu2, mu);
           const double* a = da + NB * i;

@@ -13,6 +13,7 @@
 // writes the solution over it.  Rows are fetched R at a time into registers with
 // double buffering: the next batch is in flight while the current one is swept.
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 #include <unordered_map>
 

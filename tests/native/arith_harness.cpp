@@ -77,3 +77,7 @@ void h_df_sweep(int P, int fone, int bone, long N, const double* coef, const dou
   }
 }
 }
+
+extern "C" void h_dmul_int(const double* a, const double* b, double* out, long n) {
+  for (long i = 0; i < n; ++i) out[i] = dmul_int(a[i], b[i]);
+}

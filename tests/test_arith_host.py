@@ -34,6 +34,7 @@ def H(tmp_path_factory):
     L.h_df_to_double.argtypes = [fp, fp, dp, ctypes.c_long]
     L.h_df_step.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp, fp, fp, fp]
     L.h_df_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, dp, dp, dp]
+    L.h_dmul_int.argtypes = [dp, dp, dp, ctypes.c_long]
     return L
 
 
@@ -213,3 +214,29 @@ def test_df_sweep_hyperdiffusion_workload(H):
     ref = banded.penta_solve(*fac, rhs)
     err = np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
     assert np.max(err) <= 1e-13, np.max(err)
+
+
+def test_integer_fp64_multiply_is_bit_exact(H):
+    """dmul_int (the FP64 product computed with integer instructions) must equal the
+    FP64 multiply bit for bit: random bit patterns (zeros, subnormals, infinities,
+    NaNs take the FP64 fallback), moderate values, and significands that sit on
+    rounding ties."""
+    rng = np.random.default_rng(123)
+    n = 400000
+    a = rng.integers(0, 2**63, n, dtype=np.uint64).view(np.float64) * np.where(rng.uniform(size=n) < 0.5, -1, 1)
+    b = rng.integers(0, 2**63, n, dtype=np.uint64).view(np.float64)
+    c = rng.uniform(-4, 4, n)
+    d = rng.uniform(-4, 4, n)
+    # significands ending in many ones / ties after the product
+    e = (rng.integers(0, 2**52, n, dtype=np.uint64) | np.uint64(0xFFFFFF) | np.uint64(1023 << 52)).view(np.float64)
+    f = np.ldexp(rng.uniform(1, 2, n), -20)
+    special = np.array([0.0, -0.0, 1.0, -1.0, 5e-324, 1e-308, 1e308, np.inf, -np.inf, np.nan, 2.0 ** -1022,
+                        np.nextafter(2.0, 0.0)])
+    xs = np.concatenate([a, c, e, np.repeat(special, len(special))])
+    ys = np.concatenate([b, d, f, np.tile(special, len(special))])
+    out = np.empty_like(xs)
+    with np.errstate(all="ignore"):
+        ref = xs * ys
+    H.h_dmul_int(_p(xs, ctypes.c_double), _p(ys, ctypes.c_double), _p(out, ctypes.c_double), xs.size)
+    same = (out.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(out) & np.isnan(ref))
+    assert np.all(same), (xs[~same][:3], ys[~same][:3])
