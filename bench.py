@@ -183,7 +183,7 @@ def run_reference(args):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("sweep.cu", "arith.cuh"):
+    for name in ("sweep.cu", "sweep_tile.cuh", "arith.cuh"):
         with open(os.path.join(ROOT, "paper_2107_05395_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
