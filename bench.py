@@ -412,10 +412,8 @@ def run_ours(args):
     clocks = sampler.stop()
     total_ms = t0.elapsed_time(t1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2107_05395_gb300.distributed import max_over_ranks
+    total_ms = max_over_ranks(total_ms, device="cuda")  # the slowest rank's time
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
 
@@ -446,10 +444,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, device="cuda")
 
     extras = {}
     if not args.no_extras:
