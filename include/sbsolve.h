@@ -200,6 +200,26 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
 
 /*
+ * sb_solve_batched_host -- sb_solve_batched_ex for a batch held in host memory.
+ * The batch is cut into chunks of chunk_systems systems (0 = about eight chunks);
+ * each chunk is copied to the device, solved and copied back on one of three
+ * internal streams, so both copy directions overlap the solves of neighbouring
+ * chunks.  Asynchronous: the work is ordered after prior work on `stream` and
+ * `stream` waits for all of it (synchronise it before reading x_host).
+ *   rhs_host, x_host  host arrays in the N x ld interleaved layout (may be the same
+ *                     array); page-locked memory is needed for the copies to overlap.
+ *   work              caller-owned device workspace of sb_host_workspace_bytes() bytes.
+ * Other arguments and the supported dtype/arith combinations as for
+ * sb_solve_batched_ex.  (No counterpart in the paper, whose batches live on the GPU.)
+ */
+int sb_host_workspace_bytes(const sb_factor* f, int64_t M, int64_t chunk_systems,
+                            sb_dtype rhs_dtype, sb_dtype x_dtype, size_t* bytes);
+int sb_solve_batched_host(const sb_factor* f, int transpose, const void* rhs_host,
+                          sb_dtype rhs_dtype, void* x_host, sb_dtype x_dtype, int64_t M,
+                          int64_t ld, sb_arith arith, int64_t chunk_systems, void* work,
+                          size_t work_bytes, void* stream);
+
+/*
  * Mixed precision with iterative refinement (S7 of the hot path): FP32 storage of
  * the right-hand sides, FP32 sweeps with the FP64 factors rounded to FP32, and
  * n_refine correction passes  r = b - A x,  d = A_32^{-1} r,  x += d  whose

@@ -21,5 +21,5 @@ from ._lib import (  # noqa: F401
     Shape, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run,
     sb_refine_workspace_bytes, sb_solve_batched_refined, sb_solve_batched_groups,
     sb_solve_batched_refined_noalloc, sb_rollout_workspace_bytes, sb_rollout_forward,
-    sb_rollout_backward,
+    sb_rollout_backward, sb_host_workspace_bytes, sb_solve_batched_host,
 )

@@ -71,6 +71,10 @@ SIGNATURES = {
     "sb_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _c_i64,
                                    _c_i64, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_float)]),
     "sb_build_matrix": (ctypes.c_int, [ctypes.c_int, _c_i64, ctypes.c_double, _dp]),
+    "sb_host_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "sb_solve_batched_host": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _c_i64,
+                                             _c_i64, ctypes.c_int, _c_i64, _vp, ctypes.c_size_t, _vp]),
     "sb_refine_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "sb_solve_batched_refined": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int,
                                                 _vp, ctypes.c_size_t, _vp]),
@@ -291,6 +295,25 @@ def sb_build_matrix(kind, N: int, coef: float):
     out = np.zeros((2 * P + 1) * N, dtype=np.float64)
     _check(lib().sb_build_matrix(code, N, float(coef), out.ctypes.data_as(_dp)))
     return tuple(out.reshape(2 * P + 1, N))
+
+
+def sb_host_workspace_bytes(f: Factor, M, chunk_systems=0, rhs_dtype=SB_F64, x_dtype=SB_F64):
+    out = ctypes.c_size_t()
+    _check(lib().sb_host_workspace_bytes(f.handle, M, chunk_systems, rhs_dtype, x_dtype, ctypes.byref(out)))
+    return out.value
+
+
+def sb_solve_batched_host(f: Factor, rhs_host, x_host, work, transpose=False, arith="native",
+                          chunk_systems=0, M=None, ld=None, stream=None):
+    """Solve a batch held in host memory (CPU torch tensors, ideally pinned):
+    chunked host->device copy, solve and device->host copy, overlapped on internal
+    streams; asynchronous on `stream`."""
+    M, ld = _batch_shape(rhs_host, f.N, M, ld)
+    _check(lib().sb_solve_batched_host(f.handle, 1 if transpose else 0, _dev_ptr(rhs_host),
+                                       _dtype_code(rhs_host, None), _dev_ptr(x_host), _dtype_code(x_host, None),
+                                       M, ld, _arith_code(arith), int(chunk_systems), _dev_ptr(work),
+                                       _nbytes(work), _stream_handle(stream)))
+    return x_host
 
 
 def sb_refine_workspace_bytes(f: Factor, M, ld=None):

@@ -1,0 +1,59 @@
+"""GPU parity of the host-memory solve (chunked, copy/solve overlapped on internal
+streams): pinned and pageable host arrays, chunks that do not divide the batch,
+ld > M, in-place host arrays, both arithmetic modes and the transposed solve."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import banded
+from tests.gpu_util import lib_or_skip, relerr_per_system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_or_skip()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("arith,transpose", [("native", False), ("df32", False), ("native", True)])
+@pytest.mark.parametrize("chunk", [0, 100, 1000])
+def test_host_solve_matches_oracle(env, pinned, arith, transpose, chunk):
+    sb, torch = env
+    N, M, ld = 200, 1000, 1003
+    diags = synth.random_penta_diagonals(seed=3, N=N)
+    fac = sb.sb_factor_shared_penta(*diags)
+    host = synth.rhs_normal(seed=4, N=N, M=M, ld=ld, pad_value=2.5)
+    rhs = torch.from_numpy(host.copy())
+    x = torch.full_like(rhs, 2.5)
+    if pinned:
+        rhs, x = rhs.pin_memory(), x.pin_memory()
+    work = torch.empty(sb.sb_host_workspace_bytes(fac, M, chunk), dtype=torch.uint8, device="cuda")
+    sb.sb_solve_batched_host(fac, rhs, x, work, transpose=transpose, arith=arith, chunk_systems=chunk, M=M)
+    torch.cuda.synchronize()
+    out = x.numpy()
+    fo = banded.penta_factor(*diags)
+    ref = (banded.penta_solve_adjoint if transpose else banded.penta_solve)(*fo, host[:, :M])
+    assert np.max(relerr_per_system(out[:, :M], ref)) <= 1e-12
+    assert np.all(out[:, M:] == 2.5)
+
+
+def test_host_solve_in_place_and_errors(env):
+    sb, torch = env
+    N, M = 64, 500
+    diags = synth.random_tri_diagonals(seed=5, N=N)
+    fac = sb.sb_factor_shared_tri(*diags)
+    host = synth.rhs_uniform(seed=6, N=N, M=M)
+    t = torch.from_numpy(host.copy()).pin_memory()
+    work = torch.empty(sb.sb_host_workspace_bytes(fac, M, 128), dtype=torch.uint8, device="cuda")
+    sb.sb_solve_batched_host(fac, t, t, work, chunk_systems=128)
+    torch.cuda.synchronize()
+    a, b, c = diags
+    bh, ch = banded.tri_factor(a, b, c)
+    assert np.max(relerr_per_system(t.numpy(), banded.tri_solve(a, bh, ch, host))) <= 1e-12
+    with pytest.raises(sb.SbError):  # workspace too small
+        sb.sb_solve_batched_host(fac, t, t, work[:16], chunk_systems=128)
+    dev = torch.zeros((N, M), dtype=torch.float64, device="cuda")
+    with pytest.raises(sb.SbError):  # device memory where host memory is expected
+        sb.sb_solve_batched_host(fac, dev, t, work, chunk_systems=128)
