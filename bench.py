@@ -429,6 +429,20 @@ def run_ours(args):
     def e2e_step():
         sb.sb_solve_batched_host(fac, h_rhs, h_x, hwork, arith=arith, stream=stream)
 
+    # the same workload stored and solved in FP32 (8 B per element): the path whose
+    # bound is HBM rather than the FP64 pipe
+    rhs32 = rhs.float()
+    x32 = torch.empty_like(rhs32)
+    shape32 = sb.sb_autotune(fac, rhs32, x32)
+    ms32 = time_launches(lambda: sb.sb_solve_batched(fac, rhs32, x32, stream=stream), stream,
+                         max(5, min(args.steps, 20)), 3)
+    s32 = float(np.mean(ms32)) / 1e3
+    fp32_extra = {"shape": list(shape32[0]), "ms_per_solve": s32 * 1e3,
+                  "batched_solves_per_s": 1.0 / s32,
+                  "hbm_gbs": 8.0 * N_ROWS * M_SYS / s32 / 1e9,
+                  "hbm_frac": 8.0 * N_ROWS * M_SYS / s32 / 1e9 / hbm_peak()[0]}
+    del rhs32, x32
+
     # the other arithmetic mode on the same workload, timed the same way
     other = "native" if arith == "df32" else "df32"
     other_ms = time_launches(lambda: sb.sb_solve_batched_ex(fac, rhs, x, arith=other, stream=stream),
@@ -505,6 +519,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8},
         "extras": {
             **extras,
+            "solve_fp32": fp32_extra,
             f"solve_{other}": {"shape": list(shapes[other][0]),
                                "ms_per_solve": float(np.mean(other_ms)),
                                "batched_solves_per_s": 1.0 / other_s,
