@@ -141,14 +141,44 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
                         void* stream);
 
 /*
- * Launch shape of the sweep kernels: threads per CTA (a multiple of 32 in
- * [32, 512]), resident CTAs per SM (0 = as many as fit) and systems per thread
- * (1 or 2: each thread interleaves that many independent recurrences).
+ * Solve algorithms of a batched solve.
+ *   SB_ALGO_SEQUENTIAL   one thread sweeps one system forward then back (Algorithms
+ *                        2 and 4 with the interleaved layout of section 2); the
+ *                        intermediate of the forward sweep is kept in x.
+ *   SB_ALGO_PARTITIONED  this library's own (no counterpart in the paper): a CTA
+ *                        keeps a tile of 32 systems on chip (the tile arrives by TMA
+ *                        while the previous one is solved), cut into 16 chunks of
+ *                        16/32/64 rows (512 threads) or 32 chunks of 8/16/32 rows (1024
+ *                        threads); every chunk is swept with its own factors and the
+ *                        chunks are joined through the small system of their boundary
+ *                        values, solved by parallel cyclic reduction (a SPIKE-type
+ *                        decomposition, exact up to rounding, whose spikes and reduction
+ *                        matrices depend on A only and are computed once, in FP64, with
+ *                        the factorisation).  Each rhs element is read once and each x
+ *                        element written once.  It applies to FP32 rhs with FP32 or FP64
+ *                        x in native arithmetic, 64 <= N <= 1024, rhs 16-byte aligned
+ *                        and ld a multiple of 4, when every chunk's factorisation has
+ *                        non-zero pivots; elsewhere a solve asked to use it runs the
+ *                        sequential sweeps with their default shape.
+ */
+typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
+
+/*
+ * Launch shape of a batched solve.
+ *   threads             threads per CTA: a multiple of 32 in [32, 512] for
+ *                       SB_ALGO_SEQUENTIAL; 512 (16 chunks) or 1024 (32 chunks) for
+ *                       SB_ALGO_PARTITIONED (one warp per chunk).
+ *   ctas_per_sm         cap on resident CTAs per SM (0 = as many as fit; 0 or 1 for
+ *                       SB_ALGO_PARTITIONED, which fits one).
+ *   systems_per_thread  1 or 2 for SB_ALGO_SEQUENTIAL (each thread interleaves that
+ *                       many independent recurrences); 1 for SB_ALGO_PARTITIONED.
+ *   algorithm           an sb_algo.
  */
 typedef struct {
   int threads;
   int ctas_per_sm;
   int systems_per_thread;
+  int algorithm;
 } sb_shape;
 
 /* The shape solves with this factor's (half bandwidth, N), arithmetic and dtypes
@@ -162,8 +192,8 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
                  const sb_shape* shape);
 
 /*
- * sb_autotune -- time every candidate shape (threads 64..512, CTAs/SM 0..2,
- * systems per thread 1..2) on the caller's buffers with CUDA events (one warm-up
+ * sb_autotune -- time every candidate shape (sequential: threads 64..512, CTAs/SM
+ * 0..2, systems per thread 1..2; partitioned, where it applies) on the caller's buffers with CUDA events (one warm-up
  * and the best of three launches each), store the fastest as for sb_shape_set and
  * return it in *best (and its time in *best_ms; either may be NULL).  x is
  * overwritten and must differ from rhs; arguments otherwise as for
@@ -367,6 +397,16 @@ int sb_rollout_backward(sb_stepper* st, const double* grad_CT, double* grad_C0,
                         double* grad_param_per_system, double* grad_param, int64_t M, int64_t ld,
                         int64_t nsteps, int64_t ckpt_every, sb_arith arith, void* work,
                         size_t work_bytes, void* stream);
+
+/*
+ * sb_device_timeouts -- the number of CTAs of SB_ALGO_PARTITIONED solves on `device`
+ * that gave up waiting for a tile copy since the previous call (the count is then
+ * reset to 0).  Every wait in those kernels is bounded; a CTA that gives up leaves
+ * the rest of its tiles unwritten, so a non-zero count means the outputs of the
+ * launches since the previous call are incomplete.  Synchronous (device-wide).
+ * SB_ERR_INVALID_ARG for a NULL count, SB_ERR_CUDA on a CUDA error.
+ */
+int sb_device_timeouts(int device, unsigned* count);
 
 /* Message for the last failed call on this host thread ("" if none). */
 const char* sb_last_error(void);

@@ -96,6 +96,7 @@ SIGNATURES = {
     "sb_stepper_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "sb_stepper_run": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, ctypes.c_int, _vp,
                                       ctypes.c_size_t, _vp]),
+    "sb_device_timeouts": (ctypes.c_int, [ctypes.c_int, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
 }
@@ -251,13 +252,18 @@ def sb_solve_batched_ex(f: Factor, rhs, x, transpose=False, arith="native", M=No
     return x
 
 
+SB_ALGO_SEQUENTIAL = 0
+SB_ALGO_PARTITIONED = 1
+
+
 class Shape(ctypes.Structure):
-    """sb_shape: threads per CTA, resident CTAs per SM (0 = max), systems per thread."""
+    """sb_shape: threads per CTA, resident CTAs per SM (0 = max), systems per thread,
+    algorithm (SB_ALGO_SEQUENTIAL or SB_ALGO_PARTITIONED)."""
     _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("systems_per_thread", ctypes.c_int)]
+                ("systems_per_thread", ctypes.c_int), ("algorithm", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.threads, self.ctas_per_sm, self.systems_per_thread)
+        return (self.threads, self.ctas_per_sm, self.systems_per_thread, self.algorithm)
 
 
 def _arith_code(arith):
@@ -271,13 +277,15 @@ def sb_shape_get(f: Factor, arith="native", rhs_dtype=SB_F64, x_dtype=SB_F64):
 
 
 def sb_shape_set(f: Factor, shape, arith="native", rhs_dtype=SB_F64, x_dtype=SB_F64):
+    """shape: (threads, ctas_per_sm, systems_per_thread[, algorithm]); the algorithm
+    defaults to SB_ALGO_SEQUENTIAL."""
     s = Shape(*shape)
     _check(lib().sb_shape_set(f.handle, _arith_code(arith), rhs_dtype, x_dtype, ctypes.byref(s)))
 
 
 def sb_autotune(f: Factor, rhs, x, transpose=False, arith="native", M=None, ld=None, stream=None):
     """Times every candidate launch shape on (rhs, x) and stores the fastest; returns
-    ((threads, ctas_per_sm, systems_per_thread), ms).  Overwrites x; blocking."""
+    ((threads, ctas_per_sm, systems_per_thread, algorithm), ms).  Overwrites x; blocking."""
     M, ld = _batch_shape(rhs, f.N, M, ld)
     best = Shape()
     ms = ctypes.c_float()
@@ -448,6 +456,14 @@ def sb_rollout_backward(st: Stepper, grad_CT, grad_C0, nsteps, ckpt_every, work,
         None if grad_param is None else _dev_ptr(grad_param), M, ld, int(nsteps), int(ckpt_every),
         _arith_code(arith), _dev_ptr(work), _nbytes(work), _stream_handle(stream)))
     return grad_C0
+
+
+def sb_device_timeouts(device: int = 0) -> int:
+    """CTAs of partitioned solves on ``device`` that timed out waiting for a tile
+    copy since the previous call (then reset); synchronises the device."""
+    out = ctypes.c_uint()
+    _check(lib().sb_device_timeouts(int(device), ctypes.byref(out)))
+    return out.value
 
 
 def sb_last_error() -> str:

@@ -9,6 +9,7 @@
 
 #include <cuda.h>
 
+#include "partition.h"
 #include "sb_internal.h"
 
 namespace sb {
@@ -243,6 +244,34 @@ static int upload_factor(sb_factor* f) {
   SB_CUDA(cudaMalloc(&f->arowdf, arowdf.size() * sizeof(float)));
   SB_CUDA(cudaMemcpy(f->arow64, arow.data(), arow.size() * sizeof(double), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->arowdf, arowdf.data(), arowdf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // images of the partitioned solve of A and A^T (FP32) for each variant: chunks of
+  // the shortest L that covers N (16/32/64 rows for 16 chunks, 8/16/32 for 32), N >= 64
+  for (int v = 0; v < kPartVariants; ++v) {
+    const int P = part_chunks(v);
+    int L = 0;
+    const int lens[3] = {v == 0 ? 16 : 8, v == 0 ? 32 : 16, v == 0 ? 64 : 32};
+    for (int cand : lens)
+      if (L == 0 && (int64_t)cand * P >= N) L = cand;
+    if (N < 64 || L == 0) continue;
+    for (int o = 0; o < 2; ++o) {
+      std::vector<double> dt;
+      const double* d = f->h_diag.data();
+      if (o == 1) {
+        dt = transpose_diagonals(f->P, (int)N, d);
+        d = dt.data();
+      }
+      Partition part;
+      if (!build_partition(f->P, (int)N, d, L, P, part)) continue;  // a zero pivot
+      const std::vector<double> img = partition_image(part);
+      std::vector<float> img32(img.size());
+      for (size_t k = 0; k < img.size(); ++k) img32[k] = (float)img[k];
+      SB_CUDA(cudaMalloc(&f->part_img[o][v], img32.size() * sizeof(float)));
+      SB_CUDA(cudaMemcpy(f->part_img[o][v], img32.data(), img32.size() * sizeof(float),
+                         cudaMemcpyHostToDevice));
+      f->part_L[v] = L;
+      f->part_NL[v] = part.NL;
+    }
+  }
   return SB_OK;
 }
 
@@ -256,6 +285,9 @@ static void free_factor(sb_factor* f) {
     if (f->diag64) cudaFree(f->diag64);
     if (f->arow64) cudaFree(f->arow64);
     if (f->arowdf) cudaFree(f->arowdf);
+    for (auto& per_op : f->part_img)
+      for (float* p : per_op)
+        if (p) cudaFree(p);
   }
   delete f;
 }
@@ -472,6 +504,12 @@ int sb_build_matrix(int kind, int64_t N, double coef, double* diags) {
   SB_TRY(build_matrix(kind, N, coef, v, &P));
   std::memcpy(diags, v.data(), v.size() * sizeof(double));
   return SB_OK;
+}
+
+int sb_device_timeouts(int device, unsigned* count) {
+  clear_error();
+  if (count == nullptr) return fail(SB_ERR_INVALID_ARG, "count is NULL");
+  return partition_timeouts(device, count);
 }
 
 const char* sb_last_error(void) { return g_last_error.c_str(); }

@@ -60,7 +60,13 @@ struct SweepShape {
   int threads = 256;     // threads per CTA (multiple of 32)
   int ctas_per_sm = 0;   // cap on resident CTAs per SM (0 = occupancy limit)
   int spt = 1;           // systems per thread (1 or 2)
+  int algo = SB_ALGO_SEQUENTIAL;  // sequential sweeps or the partitioned solve
 };
+
+// Partitioned-solve variants: variant v cuts the rows into part_chunks(v) chunks,
+// one warp each (CTAs of 512 or 1024 threads).
+constexpr int kPartVariants = 2;
+inline int part_chunks(int v) { return 16 << v; }
 
 }  // namespace sb
 
@@ -73,6 +79,10 @@ struct sb_factor {
   float* coefdf = nullptr;   // device: same values as (hi, lo) FP32 pairs
   double* diag64 = nullptr;  // device: the original 2P+1 diagonals, diagonal-major (d * N + i)
   double* arow64 = nullptr;  // device: A row by row, (2P+1) entries per row (offsets -P..P)
+  // device images (FP32) of the partitioned solve (partition.h) of A and A^T per
+  // variant v (part_chunks(v) chunks of part_L[v] rows); null where it does not apply
+  float* part_img[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int part_L[2] = {0, 0}, part_NL[2] = {0, 0};
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64
@@ -113,6 +123,10 @@ struct DeviceGuard {
 
 int sm_count(int device);
 
+// Resident CTAs per SM of `kernel` at (threads, smem); raises the kernel's
+// dynamic shared-memory limit to kMaxDynSmem the first time (cached).
+int kernel_occupancy(const void* kernel, int device, int threads, size_t smem, int* blocks_per_sm);
+
 // Diagonals of a workload matrix (sb_build_matrix); sets *P to 1 or 2.
 int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, int* P);
 
@@ -123,6 +137,16 @@ SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype x
 // One fused stepper step from src into dst (stepper.cu).
 int stepper_step(const sb_stepper* st, const double* src, double* dst, int64_t M, int64_t ld,
                  sb_arith arith, cudaStream_t stream);
+// The partitioned solve (partition.cu); shape.algo == SB_ALGO_PARTITIONED.
+// Variant of a partitioned shape (threads 512 -> 0, 1024 -> 1, else -1).
+int part_variant(int threads);
+bool partitioned_applies(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype,
+                         sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, int threads);
+// Reads and resets the count of partitioned-solve CTAs that timed out on `device`.
+int partition_timeouts(int device, unsigned* count);
+int launch_partitioned(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
+                       sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith,
+                       const SweepShape& shape, cudaStream_t stream);
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream);

@@ -43,36 +43,6 @@ sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t l
 
 // ----------------------------------------------------------------- launching
 
-struct Occ {
-  int blocks_per_sm = 0;
-};
-std::mutex g_occ_mu;
-std::unordered_map<uint64_t, Occ> g_occ;
-
-template <typename K>
-int prepare(K kernel, int device, int threads, size_t smem, int* blocks_per_sm) {
-  const uint64_t key = (reinterpret_cast<uint64_t>(reinterpret_cast<const void*>(kernel)) * 31u) ^
-                       ((uint64_t)smem << 20) ^ ((uint64_t)threads << 8) ^ (uint64_t)device;
-  {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    auto it = g_occ.find(key);
-    if (it != g_occ.end()) {
-      *blocks_per_sm = it->second.blocks_per_sm;
-      return SB_OK;
-    }
-  }
-  SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-  int nb = 0;
-  SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
-  if (nb < 1)
-    return fail(SB_ERR_UNSUPPORTED, "sweep kernel cannot be resident (%d threads, %zu B smem)",
-                threads, smem);
-  std::lock_guard<std::mutex> lk(g_occ_mu);
-  g_occ[key].blocks_per_sm = nb;
-  *blocks_per_sm = nb;
-  return SB_OK;
-}
-
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
 int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
            int64_t ld, const SweepShape& shape, cudaStream_t stream) {
@@ -86,7 +56,7 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   if (threads < 32 || threads > 512 || threads % 32 != 0)
     return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, 512]");
   int nb = 0;
-  SB_TRY(prepare(k, f->device, threads, smem, &nb));
+  SB_TRY(kernel_occupancy(reinterpret_cast<const void*>(k), f->device, threads, smem, &nb));
   if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
   const int64_t ntiles = (M + 32 * SPT - 1) / (32 * SPT);
   // one CTA per resident slot at most, tiles dealt round-robin over the CTAs first
@@ -122,6 +92,33 @@ int dispatch_pb(const sb_factor* f, Op op, const typename A::C* base, const void
 
 }  // namespace
 
+namespace {
+std::mutex g_occ_mu;
+std::unordered_map<uint64_t, int> g_occ;
+}  // namespace
+
+int kernel_occupancy(const void* kernel, int device, int threads, size_t smem, int* blocks_per_sm) {
+  const uint64_t key = (reinterpret_cast<uint64_t>(kernel) * 31u) ^ ((uint64_t)smem << 20) ^
+                       ((uint64_t)threads << 8) ^ (uint64_t)device;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) {
+      *blocks_per_sm = it->second;
+      return SB_OK;
+    }
+  }
+  SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+  int nb = 0;
+  SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
+  if (nb < 1)
+    return fail(SB_ERR_UNSUPPORTED, "kernel cannot be resident (%d threads, %zu B smem)", threads, smem);
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[key] = nb;
+  *blocks_per_sm = nb;
+  return SB_OK;
+}
+
 SweepShape default_shape(const sb_factor* f, sb_arith arith) {
   SweepShape s;
   s.threads = (arith == SB_ARITH_DF32) ? 128 : 256;
@@ -134,6 +131,15 @@ SweepShape default_shape(const sb_factor* f, sb_arith arith) {
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream) {
+  if (shape.algo == SB_ALGO_PARTITIONED) {
+    if (partitioned_applies(f, op, rhs, rhs_dtype, x_dtype, M, ld, arith, shape.threads))
+      return launch_partitioned(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, shape, stream);
+    // where the partition does not apply (sizes, dtypes, alignment) the sequential
+    // sweeps run with their default shape
+    return launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, default_shape(f, arith),
+                        stream);
+  }
+  if (shape.algo != SB_ALGO_SEQUENTIAL) return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape.algo);
   if (arith == SB_ARITH_NATIVE) {
     if (rhs_dtype == SB_F64 && x_dtype == SB_F64)
       return dispatch_pb<NativeArith<double>, double, double>(f, op, f->coef64, rhs, x, M, ld,

@@ -1,6 +1,6 @@
-// Launch-shape table and autotuner for the sweep kernels.
+// Launch-shape table and autotuner for the batched solves.
 //
-// A shape (threads per CTA, resident CTAs per SM, systems per thread) is looked up
+// A shape (threads per CTA, resident CTAs per SM, systems per thread, algorithm) is looked up
 // per (device, half bandwidth, N, arithmetic, rhs dtype, x dtype).  Entries come
 // from sb_shape_set (e.g. a persisted tuning cache) or from sb_autotune, which
 // times every candidate shape on the caller's buffers with CUDA events and keeps
@@ -47,6 +47,7 @@ int sb_shape_get(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
   out->threads = s.threads;
   out->ctas_per_sm = s.ctas_per_sm;
   out->systems_per_thread = s.spt;
+  out->algorithm = s.algo;
   return SB_OK;
 }
 
@@ -54,16 +55,27 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
                  const sb_shape* shape) {
   clear_error();
   if (!f || !shape) return fail(SB_ERR_INVALID_ARG, "NULL argument");
-  if (shape->threads < 32 || shape->threads > 512 || shape->threads % 32 != 0)
-    return fail(SB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512]");
+  if (shape->algorithm != SB_ALGO_SEQUENTIAL && shape->algorithm != SB_ALGO_PARTITIONED)
+    return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape->algorithm);
   if (shape->ctas_per_sm < 0 || shape->ctas_per_sm > 32)
     return fail(SB_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 32]");
-  if (shape->systems_per_thread != 1 && shape->systems_per_thread != 2)
-    return fail(SB_ERR_INVALID_ARG, "systems_per_thread must be 1 or 2");
+  if (shape->algorithm == SB_ALGO_SEQUENTIAL) {
+    if (shape->threads < 32 || shape->threads > 512 || shape->threads % 32 != 0)
+      return fail(SB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512]");
+    if (shape->systems_per_thread != 1 && shape->systems_per_thread != 2)
+      return fail(SB_ERR_INVALID_ARG, "systems_per_thread must be 1 or 2");
+  } else {
+    if (part_variant(shape->threads) < 0)
+      return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 512 or 1024 threads per CTA");
+    if (shape->systems_per_thread != 1 || shape->ctas_per_sm > 1)
+      return fail(SB_ERR_INVALID_ARG,
+                  "the partitioned solve takes systems_per_thread = 1 and ctas_per_sm 0 or 1");
+  }
   SweepShape s;
   s.threads = shape->threads;
   s.ctas_per_sm = shape->ctas_per_sm;
   s.spt = shape->systems_per_thread;
+  s.algo = shape->algorithm;
   std::lock_guard<std::mutex> lk(g_mu);
   g_table[make_key(f, arith, rhs_dtype, x_dtype)] = s;
   return SB_OK;
@@ -81,6 +93,7 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
   DeviceGuard g(f->device);
   SB_TRY(g.rc);
   cudaStream_t st = (cudaStream_t)stream;
+  const Op op = transpose ? OP_ADJOINT : OP_PRIMAL;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SB_CUDA(cudaEventCreate(&e0));
   int rc = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
@@ -88,9 +101,9 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
     cudaEventDestroy(e0);
     return rc;
   }
-  const Op op = transpose ? OP_ADJOINT : OP_PRIMAL;
   SweepShape winner = default_shape(f, arith);
   float winner_ms = 1e30f;
+  std::vector<SweepShape> cands;
   for (int spt : {1, 2})
     for (int threads : {64, 128, 256, 512})
       for (int cps : {0, 1, 2}) {
@@ -98,30 +111,41 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
         s.threads = threads;
         s.ctas_per_sm = cps;
         s.spt = spt;
-        // one warm-up launch, then the best of three timed launches
-        if (launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, s, st) != SB_OK) {
-          clear_error();
-          continue;
-        }
-        float ms_best = 1e30f;
-        bool good = true;
-        for (int rep = 0; rep < 3 && good; ++rep) {
-          good = cudaEventRecord(e0, st) == cudaSuccess &&
-                 launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, s, st) == SB_OK &&
-                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
-          float ms = 0.f;
-          if (good && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms_best = std::min(ms_best, ms);
-        }
-        if (!good) {
-          cudaGetLastError();
-          clear_error();
-          continue;
-        }
-        if (ms_best < winner_ms) {
-          winner_ms = ms_best;
-          winner = s;
-        }
+        cands.push_back(s);
       }
+  for (int threads : {512, 1024})
+    if (partitioned_applies(f, op, rhs, rhs_dtype, x_dtype, M, ld, arith, threads)) {
+      SweepShape s;
+      s.threads = threads;
+      s.ctas_per_sm = 0;
+      s.algo = SB_ALGO_PARTITIONED;
+      cands.push_back(s);
+    }
+  for (const SweepShape& s : cands) {
+    // one warm-up launch, then the best of three timed launches
+    if (launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, s, st) != SB_OK) {
+      clear_error();
+      continue;
+    }
+    float ms_best = 1e30f;
+    bool good = true;
+    for (int rep = 0; rep < 3 && good; ++rep) {
+      good = cudaEventRecord(e0, st) == cudaSuccess &&
+             launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, s, st) == SB_OK &&
+             cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      if (good && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms_best = std::min(ms_best, ms);
+    }
+    if (!good) {
+      cudaGetLastError();
+      clear_error();
+      continue;
+    }
+    if (ms_best < winner_ms) {
+      winner_ms = ms_best;
+      winner = s;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (winner_ms >= 1e30f) return fail(SB_ERR_CUDA, "no candidate shape could be launched");
@@ -133,6 +157,7 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
     best->threads = winner.threads;
     best->ctas_per_sm = winner.ctas_per_sm;
     best->systems_per_thread = winner.spt;
+    best->algorithm = winner.algo;
   }
   if (best_ms) *best_ms = winner_ms;
   return SB_OK;

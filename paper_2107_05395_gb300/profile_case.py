@@ -25,7 +25,7 @@ def main():
     ap.add_argument("--arith", choices=["native", "df32"], default="native")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape first")
-    ap.add_argument("--shape", default=None, help="threads,ctas_per_sm,systems_per_thread")
+    ap.add_argument("--shape", default=None, help="threads,ctas_per_sm,systems_per_thread[,algorithm]")
     args = ap.parse_args()
 
     import torch

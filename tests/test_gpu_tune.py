@@ -24,7 +24,7 @@ def test_every_shape_matches_oracle(env, arith, shape):
     diags = synth.random_penta_diagonals(seed=7, N=N)
     fac = sb.sb_factor_shared_penta(*diags)
     sb.sb_shape_set(fac, shape, arith=arith)
-    assert sb.sb_shape_get(fac, arith=arith) == shape
+    assert sb.sb_shape_get(fac, arith=arith) == shape + (0,)
     rhs = synth.rhs_normal(seed=8, N=N, M=M, ld=M + 3, pad_value=7.0)
     d = to_dev(rhs, torch)
     x = torch.full_like(d, 7.0)
@@ -59,6 +59,7 @@ def test_autotune_stores_a_valid_shape(env):
 def test_bad_shapes_rejected(env):
     sb, _ = env
     fac = sb.sb_factor_shared_tri(*synth.random_tri_diagonals(seed=1, N=8))
-    for bad in [(48, 0, 1), (1024, 0, 1), (64, -1, 1), (64, 0, 3)]:
+    for bad in [(48, 0, 1), (1024, 0, 1), (64, -1, 1), (64, 0, 3), (64, 0, 1, 1), (256, 0, 2, 1),
+                (256, 0, 1, 7)]:
         with pytest.raises(sb.SbError):
             sb.sb_shape_set(fac, bad)
