@@ -439,7 +439,7 @@ def run_ours(args):
     for algo, name in ((sb.SB_ALGO_SEQUENTIAL, "sequential"), (sb.SB_ALGO_PARTITIONED, "partitioned")):
         best = None
         for shp in ([(t, c, 1, algo) for t in (128, 256, 512) for c in (0, 1)] if algo == 0
-                    else [(t, c, 1, algo) for t in (256, 512) for c in (0, 1, 2)]):
+                    else [(t, 0, 1, algo) for t in (512, 1024)]):
             sb.sb_shape_set(fac, shp, rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32)
             try:
                 t = float(np.min(time_launches(lambda: sb.sb_solve_batched(fac, rhs32, x32, stream=stream),

@@ -160,6 +160,10 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
  *                        and ld a multiple of 4, when every chunk's factorisation has
  *                        non-zero pivots; elsewhere a solve asked to use it runs the
  *                        sequential sweeps with their default shape.
+ *                        With 128-thread CTAs it is the FP64 form for latency-bound
+ *                        batches: tiles of 8 systems cut into 16 chunks of 8/16/32 rows
+ *                        (32 <= N <= 512), FP64 rhs and x, native arithmetic, the
+ *                        boundary system solved by block Thomas; same fallback.
  */
 typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
 
@@ -167,7 +171,8 @@ typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
  * Launch shape of a batched solve.
  *   threads             threads per CTA: a multiple of 32 in [32, 512] for
  *                       SB_ALGO_SEQUENTIAL; 512 (16 chunks) or 1024 (32 chunks) for
- *                       SB_ALGO_PARTITIONED (one warp per chunk).
+ *                       SB_ALGO_PARTITIONED with FP32 rhs (one warp per chunk), 128 for
+ *                       its FP64 form.
  *   ctas_per_sm         cap on resident CTAs per SM (0 = as many as fit; 0 or 1 for
  *                       SB_ALGO_PARTITIONED, which fits one).
  *   systems_per_thread  1 or 2 for SB_ALGO_SEQUENTIAL (each thread interleaves that

@@ -272,6 +272,30 @@ static int upload_factor(sb_factor* f) {
       f->part_NL[v] = part.NL;
     }
   }
+  // FP64 block-Thomas images of the small-tile FP64 partitioned solve: kPart64Chunks
+  // chunks of the shortest L in {8, 16, 32} that covers N, for N >= 32
+  {
+    int L64 = 0;
+    for (int cand : {8, 16, 32})
+      if (L64 == 0 && (int64_t)cand * kPart64Chunks >= N) L64 = cand;
+    if (N >= 32 && L64 > 0) {
+      for (int o = 0; o < 2; ++o) {
+        std::vector<double> dt;
+        const double* d = f->h_diag.data();
+        if (o == 1) {
+          dt = transpose_diagonals(f->P, (int)N, d);
+          d = dt.data();
+        }
+        Partition part;
+        if (!build_partition(f->P, (int)N, d, L64, kPart64Chunks, part)) continue;
+        const std::vector<double> img = partition_image_thomas(part);
+        SB_CUDA(cudaMalloc(&f->part64_img[o], img.size() * sizeof(double)));
+        SB_CUDA(cudaMemcpy(f->part64_img[o], img.data(), img.size() * sizeof(double),
+                           cudaMemcpyHostToDevice));
+        f->part64_L = L64;
+      }
+    }
+  }
   return SB_OK;
 }
 
@@ -288,6 +312,8 @@ static void free_factor(sb_factor* f) {
     for (auto& per_op : f->part_img)
       for (float* p : per_op)
         if (p) cudaFree(p);
+    for (double* p : f->part64_img)
+      if (p) cudaFree(p);
   }
   delete f;
 }

@@ -48,6 +48,12 @@ struct Partition {
   // reduced system, per boundary k < K: T0 (Q x Q); per level l and boundary k:
   // M0 (Q x Q), M1 (Q x PB), M2 (Q x PB); all row-major, k-major within a level
   std::vector<double> T0, M0, M1, M2;
+  // the same reduced system factored for block Thomas (block LU without pivoting),
+  // per boundary k: E_k = Lo_k G_{k-1}^{-1} (its first PB rows, PB x Q), H_k = G_k^{-1}
+  // (Q x Q) and J_k = G_k^{-1} Up_k (its last PB columns, Q x PB), G_0 = D_0,
+  // G_k = D_k - E_k Up_{k-1}; per system q_k = r_k - E_k q_{k-1} (rows 0..PB-1),
+  // then z_{K-1} = H q, z_k = H_k q_k - J_k z_{k+1}[PB:Q]
+  std::vector<double> E, H, J;
   int Q() const { return 2 * PB; }
   int K() const { return P - 1; }
 };
@@ -189,6 +195,10 @@ inline bool build_partition(int PB, int N, const double* diag, int L, int P, Par
   p.M1.assign((size_t)p.NL * Kz * Q * PB, 0.0);
   p.M2.assign((size_t)p.NL * Kz * Q * PB, 0.0);
   std::vector<std::vector<double>> a(Kz, std::vector<double>(Q * Q, 0.0)), cc = a;
+  p.E.assign(Kz * PB * Q, 0.0);
+  p.H.assign(Kz * Q * Q, 0.0);
+  p.J.assign(Kz * Q * PB, 0.0);
+  std::vector<double> Ginv_prev, Up_prev;
   for (int k = 0; k < K; ++k) {
     const int ek = (k + 1) * L;  // first row of chunk k+1
     std::vector<double> D(Q * Q, 0.0), Lo(Q * Q, 0.0), Up(Q * Q, 0.0);
@@ -202,6 +212,22 @@ inline bool build_partition(int PB, int N, const double* diag, int L, int P, Par
         Lo[u * Q + v] = p.W[(size_t)PB * rt + v];              // Wb_k on z_{k-1}[0:PB]
         Up[(PB + u) * Q + PB + v] = p.V[(size_t)PB * rh + v];  // Vt_{k+1} on z_{k+1}[PB:Q]
       }
+    }
+    {  // block Thomas factors
+      std::vector<double> G = D;
+      if (k > 0) {
+        const std::vector<double> Ek = matmul(Lo, Ginv_prev, Q), EU = matmul(Ek, Up_prev, Q);
+        for (int t = 0; t < Q * Q; ++t) G[t] -= EU[t];
+        for (int u = 0; u < PB; ++u)
+          for (int v = 0; v < Q; ++v) p.E[((size_t)k * PB + u) * Q + v] = Ek[u * Q + v];
+      }
+      if (!invert(G, Q)) return false;
+      const std::vector<double> GU = matmul(G, Up, Q);
+      std::copy(G.begin(), G.end(), p.H.begin() + (size_t)k * Q * Q);
+      for (int u = 0; u < Q; ++u)
+        for (int v = 0; v < PB; ++v) p.J[((size_t)k * Q + u) * PB + v] = GU[u * Q + PB + v];
+      Ginv_prev = G;
+      Up_prev = Up;
     }
     if (!invert(D, Q)) return false;
     std::copy(D.begin(), D.end(), p.T0.begin() + (size_t)k * Q * Q);
@@ -243,12 +269,14 @@ inline bool build_partition(int PB, int N, const double* diag, int L, int P, Par
     a = na;
     cc = nc;
   }
-  return all_finite(p.T0) && all_finite(p.M0) && all_finite(p.M1) && all_finite(p.M2);
+  return all_finite(p.T0) && all_finite(p.M0) && all_finite(p.M1) && all_finite(p.M2) &&
+         all_finite(p.E) && all_finite(p.H) && all_finite(p.J);
 }
 
 // Reference application of the partitioned solve to one right-hand side (length N),
-// in FP64 and in the order of operations of the device kernel (host tests).
-inline void partition_solve_ref(const Partition& p, const double* b, double* x) {
+// in FP64 and in the order of operations of the device kernels (host tests); the
+// boundary system by cyclic reduction, or by block Thomas when `thomas`.
+inline void partition_solve_ref(const Partition& p, const double* b, double* x, bool thomas = false) {
   const int PB = p.PB, P = p.P, L = p.L, Q = 2 * PB, W = PB + 1, K = P - 1, NP = P * L;
   std::vector<double> y(NP, 0.0);
   for (int i = 0; i < p.N; ++i) y[i] = b[i];
@@ -276,6 +304,33 @@ inline void partition_solve_ref(const Partition& p, const double* b, double* x) 
     }
   }
   std::vector<double> d((size_t)std::max(K, 0) * Q, 0.0);
+  if (thomas) {
+    for (int k = 0; k < K; ++k) {  // q_k = r_k - E_k q_{k-1}
+      const int ek = (k + 1) * L;
+      double q[4];
+      for (int u = 0; u < PB; ++u) {
+        q[u] = y[ek - PB + u];
+        q[PB + u] = y[ek + u];
+      }
+      if (k > 0)
+        for (int u = 0; u < PB; ++u)
+          for (int t = 0; t < Q; ++t)
+            q[u] = std::fma(-p.E[((size_t)k * PB + u) * Q + t], d[(size_t)(k - 1) * Q + t], q[u]);
+      for (int u = 0; u < Q; ++u) d[(size_t)k * Q + u] = q[u];
+    }
+    for (int k = K - 1; k >= 0; --k) {  // z_k = H_k q_k - J_k z_{k+1}[PB:Q]
+      double z[4];
+      for (int u = 0; u < Q; ++u) {
+        double t = 0;
+        for (int v = 0; v < Q; ++v) t = std::fma(p.H[((size_t)k * Q + u) * Q + v], d[(size_t)k * Q + v], t);
+        if (k + 1 < K)
+          for (int v = 0; v < PB; ++v)
+            t = std::fma(-p.J[((size_t)k * Q + u) * PB + v], d[(size_t)(k + 1) * Q + PB + v], t);
+        z[u] = t;
+      }
+      for (int u = 0; u < Q; ++u) d[(size_t)k * Q + u] = z[u];
+    }
+  } else {
   for (int k = 0; k < K; ++k) {
     const int ek = (k + 1) * L;
     double r[4];
@@ -305,6 +360,7 @@ inline void partition_solve_ref(const Partition& p, const double* b, double* x) 
       }
     }
     d = nd;
+  }
   }
   for (int c = 0; c < P; ++c) {
     const int s = c * L;
@@ -396,6 +452,53 @@ inline std::vector<double> transpose_diagonals(int PB, int N, const double* diag
       if (j >= 0 && j < N) t[(size_t)(o + PB) * N + i] = diag[(size_t)(PB - o) * N + j];
     }
   return t;
+}
+
+// FP64 image for the small-tile FP64 kernel (scalar records, block Thomas factors).
+// Sections, each starting on a multiple of 4 elements:
+//   fwd  P L rows of FW = (PB == 2 ? 4 : 2): F0, F1[, F2, 0];  bwd  P L rows of PB: B1[, B2]
+//   cor  P L rows of Q: W_0[, W_1], V_0[, V_1]
+//   E    K x PB x Q;  H  K x Q x Q;  J  K x Q x PB  (row-major, boundary-major)
+struct PartLayoutT {
+  int fwd, bwd, cor, E, H, J, total;
+};
+
+inline PartLayoutT part_layout_thomas(int PB, int L, int P) {
+  const int Q = 2 * PB, FW = PB == 2 ? 4 : 2, NP = P * L, K = P - 1;
+  PartLayoutT l;
+  int o = 0;
+  l.fwd = o;
+  o = round4(o + NP * FW);
+  l.bwd = o;
+  o = round4(o + NP * PB);
+  l.cor = o;
+  o = round4(o + NP * Q);
+  l.E = o;
+  o = round4(o + K * PB * Q);
+  l.H = o;
+  o = round4(o + K * Q * Q);
+  l.J = o;
+  o = round4(o + K * Q * PB);
+  l.total = o;
+  return l;
+}
+
+inline std::vector<double> partition_image_thomas(const Partition& p) {
+  const int PB = p.PB, W = PB + 1, FW = PB == 2 ? 4 : 2, Q = 2 * PB, NP = p.P * p.L;
+  const PartLayoutT l = part_layout_thomas(PB, p.L, p.P);
+  std::vector<double> img(l.total, 0.0);
+  for (int i = 0; i < NP; ++i) {
+    for (int k = 0; k < W; ++k) img[l.fwd + i * FW + k] = p.fw[(size_t)W * i + k];
+    for (int k = 0; k < PB; ++k) {
+      img[l.bwd + i * PB + k] = p.bw[(size_t)PB * i + k];
+      img[l.cor + i * Q + k] = p.W[(size_t)PB * i + k];
+      img[l.cor + i * Q + PB + k] = p.V[(size_t)PB * i + k];
+    }
+  }
+  std::copy(p.E.begin(), p.E.end(), img.begin() + l.E);
+  std::copy(p.H.begin(), p.H.end(), img.begin() + l.H);
+  std::copy(p.J.begin(), p.J.end(), img.begin() + l.J);
+  return img;
 }
 
 }  // namespace sb

@@ -83,6 +83,10 @@ struct sb_factor {
   // variant v (part_chunks(v) chunks of part_L[v] rows); null where it does not apply
   float* part_img[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int part_L[2] = {0, 0}, part_NL[2] = {0, 0};
+  // FP64 images (block Thomas form) of the small-tile FP64 partitioned solve of A and
+  // A^T: 16 chunks of part64_L rows; null where it does not apply
+  double* part64_img[2] = {nullptr, nullptr};
+  int part64_L = 0;
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64
@@ -138,6 +142,13 @@ SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype x
 int stepper_step(const sb_stepper* st, const double* src, double* dst, int64_t M, int64_t ld,
                  sb_arith arith, cudaStream_t stream);
 // The partitioned solve (partition.cu); shape.algo == SB_ALGO_PARTITIONED.
+// The small-tile FP64 partitioned solve (partition64.cu): 128-thread CTAs, 16 chunks.
+constexpr int kPart64Threads = 128;
+constexpr int kPart64Chunks = 16;
+bool partitioned64_applies(const sb_factor* f, Op op, sb_dtype rhs_dtype, sb_dtype x_dtype,
+                           int64_t M, sb_arith arith);
+int launch_partitioned64(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M, int64_t ld,
+                         const SweepShape& shape, cudaStream_t stream);
 // Variant of a partitioned shape (threads 512 -> 0, 1024 -> 1, else -1).
 int part_variant(int threads);
 bool partitioned_applies(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype,

@@ -131,6 +131,12 @@ SweepShape default_shape(const sb_factor* f, sb_arith arith) {
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream) {
+  if (shape.algo == SB_ALGO_PARTITIONED && shape.threads == kPart64Threads) {
+    if (partitioned64_applies(f, op, rhs_dtype, x_dtype, M, arith))
+      return launch_partitioned64(f, op, rhs, x, M, ld, shape, stream);
+    return launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, default_shape(f, arith),
+                        stream);
+  }
   if (shape.algo == SB_ALGO_PARTITIONED) {
     if (partitioned_applies(f, op, rhs, rhs_dtype, x_dtype, M, ld, arith, shape.threads))
       return launch_partitioned(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, shape, stream);

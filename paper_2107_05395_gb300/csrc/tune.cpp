@@ -4,7 +4,8 @@
 // per (device, half bandwidth, N, arithmetic, rhs dtype, x dtype).  Entries come
 // from sb_shape_set (e.g. a persisted tuning cache) or from sb_autotune, which
 // times every candidate shape on the caller's buffers with CUDA events and keeps
-// the fastest.  Without an entry the built-in default of sweep.cu is used.
+// the fastest.  Without an entry, FP32 right-hand sides in native arithmetic use the
+// partitioned solve where it applies and everything else the default of sweep.cu.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -30,6 +31,17 @@ SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype x
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_table.find(make_key(f, arith, rt, xt));
   if (it != g_table.end()) return it->second;
+  // FP32 right-hand sides in native arithmetic default to the partitioned solve where
+  // the factor has its data (the launcher falls back to the sweeps per call where it
+  // does not apply)
+  if (arith == SB_ARITH_NATIVE && rt == SB_F32 && (f->part_img[0][0] || f->part_img[1][0])) {
+    SweepShape s;
+    s.threads = 512;
+    s.ctas_per_sm = 0;
+    s.spt = 1;
+    s.algo = SB_ALGO_PARTITIONED;
+    return s;
+  }
   return default_shape(f, arith);
 }
 
@@ -65,8 +77,8 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
     if (shape->systems_per_thread != 1 && shape->systems_per_thread != 2)
       return fail(SB_ERR_INVALID_ARG, "systems_per_thread must be 1 or 2");
   } else {
-    if (part_variant(shape->threads) < 0)
-      return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 512 or 1024 threads per CTA");
+    if (part_variant(shape->threads) < 0 && shape->threads != kPart64Threads)
+      return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 128, 512 or 1024 threads per CTA");
     if (shape->systems_per_thread != 1 || shape->ctas_per_sm > 1)
       return fail(SB_ERR_INVALID_ARG,
                   "the partitioned solve takes systems_per_thread = 1 and ctas_per_sm 0 or 1");
@@ -113,6 +125,13 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
         s.spt = spt;
         cands.push_back(s);
       }
+  if (partitioned64_applies(f, op, rhs_dtype, x_dtype, M, arith)) {
+    SweepShape s;
+    s.threads = kPart64Threads;
+    s.ctas_per_sm = 0;
+    s.algo = SB_ALGO_PARTITIONED;
+    cands.push_back(s);
+  }
   for (int threads : {512, 1024})
     if (partitioned_applies(f, op, rhs, rhs_dtype, x_dtype, M, ld, arith, threads)) {
       SweepShape s;

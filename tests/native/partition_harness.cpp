@@ -11,9 +11,10 @@ extern "C" {
 // Solves A x_m = b_m (transpose = 0) or A^T x_m = b_m (transpose = 1) for the M
 // systems of the interleaved array b (row i of system m at i * M + m) with P chunks
 // of L rows.  diag: 2PB+1 diagonals, diagonal-major.  Returns the number of cyclic
-// reduction levels, or -1 when the partition cannot be built.
+// reduction levels, or -1 when the partition cannot be built.  thomas != 0 solves the
+// boundary system with the block Thomas factors instead of cyclic reduction.
 int h_partition_solve(int PB, int N, const double* diag, int L, int P, int transpose, long M,
-                      const double* b, double* x) {
+                      const double* b, double* x, int thomas) {
   std::vector<double> dt;
   const double* d = diag;
   if (transpose) {
@@ -25,7 +26,7 @@ int h_partition_solve(int PB, int N, const double* diag, int L, int P, int trans
   std::vector<double> bm(N), xm(N);
   for (long m = 0; m < M; ++m) {
     for (int i = 0; i < N; ++i) bm[i] = b[(long)i * M + m];
-    partition_solve_ref(p, bm.data(), xm.data());
+    partition_solve_ref(p, bm.data(), xm.data(), thomas != 0);
     for (int i = 0; i < N; ++i) x[(long)i * M + m] = xm[i];
   }
   return p.NL;

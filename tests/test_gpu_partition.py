@@ -171,3 +171,57 @@ def test_autotune_fp32_headline_shape_is_correct(env):
     torch.cuda.synchronize()
     ref = oracle(diags, to_host(rhs[:, :256]).astype(np.float64), False)
     assert np.max(relerr_per_system(to_host(x[:, :256]).astype(np.float64), ref)) <= TOL32
+
+
+FP64 = (128, 0, 1, 1)  # the small-tile FP64 form of SB_ALGO_PARTITIONED
+
+MATS64 = {
+    "tri_diffusion_N256_M1024": (lambda: matrices.diffusion_matrix(256, 0.5), 1024),
+    "penta_random_N500": (lambda: synth.random_penta_diagonals(seed=15, N=500), 1000),
+    "hinged_N512": (lambda: matrices.hyperdiffusion_matrix(512, 0.25), 777),
+    "ch_N256": (lambda: matrices.ch_matrix(256, 0.0166), 333),
+    "tri_random_N40_padded": (lambda: synth.random_tri_diagonals(seed=16, N=40), 65),
+    "penta_random_N100_empty_chunks": (lambda: synth.random_penta_diagonals(seed=17, N=100), 9),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS64))
+def test_partitioned_fp64_matches_oracle(env, name):
+    """The FP64 form against the FP64 oracle at the FP64 tolerance, A and A^T, ragged
+    tiles of 8 systems, padding columns untouched, then in place."""
+    sb, torch = env
+    make, M = MATS64[name]
+    diags = make()
+    N = len(diags[0])
+    ld = M + 3
+    fac = factor(sb, diags)
+    sb.sb_shape_set(fac, FP64)
+    assert sb.sb_shape_get(fac) == FP64
+    rhs = synth.rhs_normal(seed=19, N=N, M=M, ld=ld, pad_value=CANARY)
+    d = to_dev(rhs, torch)
+    x = torch.full_like(d, CANARY)
+    for adjoint in (False, True):
+        sb.sb_solve_batched_ex(fac, d, x, transpose=adjoint, M=M)
+        torch.cuda.synchronize()
+        out = to_host(x)
+        err = np.max(relerr_per_system(out[:, :M], oracle(diags, rhs[:, :M], adjoint)))
+        assert err <= TOL64, (name, adjoint, err)
+        assert np.all(out[:, M:] == CANARY)
+    sb.sb_solve_batched(fac, d, M=M, ld=ld)  # in place
+    torch.cuda.synchronize()
+    out = to_host(d)
+    assert np.max(relerr_per_system(out[:, :M], oracle(diags, rhs[:, :M], False))) <= TOL64
+    assert np.all(out[:, M:] == CANARY)
+
+
+def test_partitioned_fp64_falls_back_outside_its_range(env):
+    sb, torch = env
+    diags = synth.random_penta_diagonals(seed=18, N=1000)  # N > 512: no FP64 partition
+    fac = factor(sb, diags)
+    sb.sb_shape_set(fac, FP64)
+    rhs = synth.rhs_normal(seed=20, N=1000, M=50)
+    d = to_dev(rhs, torch)
+    x = torch.empty_like(d)
+    sb.sb_solve_batched(fac, d, x)
+    torch.cuda.synchronize()
+    assert np.max(relerr_per_system(to_host(x), oracle(diags, rhs, False))) <= TOL64

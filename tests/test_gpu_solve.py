@@ -78,7 +78,10 @@ def test_penta_random_fp64(env, N, M, ld, adjoint):
 
 
 @pytest.mark.parametrize("kind", ["tri", "penta"])
-def test_fp32_storage_and_arithmetic(env, kind):
+@pytest.mark.parametrize("algorithm", ["default", "sequential"])
+def test_fp32_storage_and_arithmetic(env, kind, algorithm):
+    """FP32 storage and arithmetic; the default shape of an FP32 solve is the
+    partitioned algorithm, the sequential sweeps are forced once."""
     sb, torch = env
     N, M = 300, 515
     if kind == "tri":
@@ -89,6 +92,10 @@ def test_fp32_storage_and_arithmetic(env, kind):
         diags = synth.random_penta_diagonals(seed=5, N=N)
         fac = sb.sb_factor_shared_penta(*diags)
         orc = oracle_penta
+    if algorithm == "sequential":
+        sb.sb_shape_set(fac, (256, 0, 1, 0), rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32)
+    else:
+        assert sb.sb_shape_get(fac, rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32)[3] == 1
     rhs = synth.rhs_uniform(seed=6, N=N, M=M, dtype=np.float32)
     for adj in (False, True):
         x = run_solve(sb, torch, fac, rhs, M, dtype=np.float32, adjoint=adj)
@@ -218,7 +225,8 @@ def test_df32_fp64_io_matches_oracle(env, kind, N, M, ld, adjoint):
 
 
 @pytest.mark.parametrize("kind", ["tri", "penta"])
-def test_fp32_rhs_fp64_solution(env, kind):
+@pytest.mark.parametrize("algorithm", ["default", "sequential"])
+def test_fp32_rhs_fp64_solution(env, kind, algorithm):
     """FP32-stored right-hand side solved into an FP64 solution: with df32
     arithmetic to FP64 accuracy of the promoted input, with native FP32 to FP32
     accuracy."""
@@ -232,6 +240,8 @@ def test_fp32_rhs_fp64_solution(env, kind):
         diags = tuple(sb.sb_build_matrix("hinged", N, 0.25))
         fac = sb.sb_factor_shared_penta(*diags)
         A = steppers.SharedPenta(*matrices.hyperdiffusion_matrix(N, 0.25, "hinged"))
+    if algorithm == "sequential":
+        sb.sb_shape_set(fac, (256, 0, 1, 0), rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F64)
     b32 = synth.rhs_uniform(seed=3, N=N, M=M, dtype=np.float32)
     ref = steppers.solve_fp32_rhs(A, b32)
     x = run_ex(sb, torch, fac, b32, M, np.float32, np.float64, "df32")

@@ -35,7 +35,7 @@ def H(tmp_path_factory):
     dp = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     L.h_partition_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
-                                    ctypes.c_int, ctypes.c_long, dp, dp]
+                                    ctypes.c_int, ctypes.c_long, dp, dp, ctypes.c_int]
     L.h_partition_image.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
                                     ctypes.c_int, ip]
     return L
@@ -49,13 +49,14 @@ def _diag_major(diags):
     return np.ascontiguousarray(np.concatenate([np.asarray(d, np.float64) for d in diags]))
 
 
-def part_solve(H, diags, L, P, b, transpose=False):
+def part_solve(H, diags, L, P, b, transpose=False, thomas=False):
     PB = (len(diags) - 1) // 2
     N, M = b.shape
     dm = _diag_major(diags)
     b = np.ascontiguousarray(b, np.float64)
     x = np.empty_like(b)
-    NL = H.h_partition_solve(PB, N, _dp(dm), L, P, 1 if transpose else 0, M, _dp(b), _dp(x))
+    NL = H.h_partition_solve(PB, N, _dp(dm), L, P, 1 if transpose else 0, M, _dp(b), _dp(x),
+                             1 if thomas else 0)
     assert NL >= 0
     return x, NL
 
@@ -91,11 +92,12 @@ CASES = [
 
 @pytest.mark.parametrize("name,make,L,P", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_partitioned_solve_matches_sequential_oracle(H, name, make, L, P, transpose):
+@pytest.mark.parametrize("reduced", ["cyclic_reduction", "block_thomas"])
+def test_partitioned_solve_matches_sequential_oracle(H, name, make, L, P, transpose, reduced):
     diags = make()
     N = len(diags[0])
     b = synth.rhs_uniform(seed=9, N=N, M=5)
-    x, NL = part_solve(H, diags, L, P, b, transpose)
+    x, NL = part_solve(H, diags, L, P, b, transpose, thomas=reduced == "block_thomas")
     assert NL == int(np.ceil(np.log2(P - 1))) if P > 2 else NL == 0
     ref = oracle_solve(diags, b, transpose)
     # both are backward-stable solves of a well-conditioned system; rounding only
@@ -166,7 +168,7 @@ def test_zero_pivot_is_reported(H):
     b0 = np.ones((40, 1))
     x = np.empty_like(b0)
     dm = _diag_major((a, b, c, d, e))
-    assert H.h_partition_solve(2, 40, _dp(dm), 10, 4, 0, 1, _dp(b0), _dp(x)) == -1
+    assert H.h_partition_solve(2, 40, _dp(dm), 10, 4, 0, 1, _dp(b0), _dp(x), 0) == -1
     # too few chunks to cover the rows
     dm2 = _diag_major(synth.random_penta_diagonals(10, 40))
-    assert H.h_partition_solve(2, 40, _dp(dm2), 8, 4, 0, 1, _dp(b0), _dp(x)) == -1
+    assert H.h_partition_solve(2, 40, _dp(dm2), 8, 4, 0, 1, _dp(b0), _dp(x), 0) == -1
