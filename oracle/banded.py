@@ -21,6 +21,7 @@ import numpy as np
 
 __all__ = [
     "tri_factor", "tri_solve", "tri_solve_adjoint",
+    "tri_periodic_factor", "tri_periodic_solve", "tri_periodic_solve_adjoint", "tri_periodic_dense",
     "penta_factor", "penta_solve", "penta_solve_adjoint",
     "tri_dense", "penta_dense",
 ]
@@ -110,6 +111,73 @@ def tri_dense(a, b, c):
         A[i - 1, i] = c[i - 1]
     return A
 
+
+
+# ----------------------------------------------------------------------------
+# Periodic tridiagonal (section 3.3, "Periodic Tridiagonal Matrix")
+# ----------------------------------------------------------------------------
+
+def tri_periodic_dense(a, b, c):
+    """Dense periodic tridiagonal matrix: the three diagonals of :func:`tri_dense`
+    plus the two corner entries of section 3.3, A[0, N-1] = a_0 (row 0's
+    sub-diagonal coefficient wraps around) and A[N-1, 0] = c_{N-1} (row N-1's
+    super-diagonal coefficient wraps around).  N >= 3."""
+    N = len(b)
+    if N < 3:
+        raise ValueError("a periodic tridiagonal matrix needs N >= 3")
+    A = tri_dense(a, b, c)
+    A[0, N - 1] = a[0]
+    A[N - 1, 0] = c[N - 1]
+    return A
+
+
+def tri_periodic_factor(a, b, c):
+    """Section 3.3: write A = A' + u v^T with
+
+        u = (-b_0, 0, ..., 0, c_{N-1})^T,   v = (1, 0, ..., 0, -a_0 / b_0)^T,
+
+    so that A' is the plain tridiagonal matrix with b'_0 = 2 b_0 and
+    b'_{N-1} = b_{N-1} + a_0 c_{N-1} / b_0 and no corner entries (the section's
+    constant-coefficient u, v and A' with the coefficients taken per row).  A' is
+    factored by section 3.1 once, and z = A'^{-1} u is solved once, as the section
+    says ("need only be performed once").  Returns a dict with the factors of A',
+    u, v and z."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    N = b.shape[0]
+    if N < 3:
+        raise ValueError("a periodic tridiagonal matrix needs N >= 3")
+    u = np.zeros(N)
+    v = np.zeros(N)
+    u[0], u[N - 1] = -b[0], c[N - 1]
+    v[0], v[N - 1] = 1.0, -a[0] / b[0]
+    ap, bp, cp = a.copy(), b.copy(), c.copy()
+    ap[0] = 0.0
+    cp[N - 1] = 0.0
+    bp[0] = b[0] - u[0] * v[0]
+    bp[N - 1] = b[N - 1] - u[N - 1] * v[N - 1]
+    bh, ch = tri_factor(ap, bp, cp)
+    z = tri_solve(ap, bh, ch, u[:, None])[:, 0]
+    return {"a": ap, "bh": bh, "ch": ch, "u": u, "v": v, "z": z}
+
+
+def tri_periodic_solve(fac, d):
+    """Solve A x = d for every column of ``d`` (section 3.3):
+        A' y = d,   x = y - ((v . y) / (1 + v . z)) z."""
+    y = tri_solve(fac["a"], fac["bh"], fac["ch"], d)
+    vy = fac["v"] @ y
+    return y - np.outer(fac["z"], vy / (1.0 + fac["v"] @ fac["z"]))
+
+
+def tri_periodic_solve_adjoint(fac, g):
+    """Solve A^T y = g (no counterpart in the paper): A^T = A'^T + v u^T, so with
+    the same factors of A', w = A'^{-T} g, z' = A'^{-T} v and
+        y = w - ((u . w) / (1 + u . z')) z'."""
+    w = tri_solve_adjoint(fac["a"], fac["bh"], fac["ch"], g)
+    zt = tri_solve_adjoint(fac["a"], fac["bh"], fac["ch"], fac["v"][:, None])[:, 0]
+    uw = fac["u"] @ w
+    return w - np.outer(zt, uw / (1.0 + fac["u"] @ zt))
 
 # ----------------------------------------------------------------------------
 # Pentadiagonal (section 4.1, "Pentadiagonal Inversion Algorithm"; Algorithms 3-4)

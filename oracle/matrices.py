@@ -19,6 +19,9 @@ use the non-periodic closures below):
   C = C'' = 0 at both ends); corner entries 5, next rows (-4, 6, -4, 1).
 * ``truncated``  -- D4 is the plain Toeplitz (1, -4, 6, -4, 1) cut at the edges
   (corner entries 6).
+* ``periodic``   -- the paper's own closure (sections 3.2 and 3.3): row 0's left
+  neighbour is row N-1 and row N-1's right neighbour is row 0; the two wrapped
+  coefficients sit in sub[0] and sup[N-1] (the corners of section 3.3).
 * ``noflux``     -- cell-centred Neumann closure: D2_N has rows (-1, 1),
   (1, -2, 1), ..., (1, -1) (even reflection of the ghost cell), and
   D4_N = D2_N @ D2_N.  Every column of D2_N sums to zero, so sum(C) is
@@ -29,9 +32,9 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "d2_dirichlet", "d2_noflux", "square_tridiag", "d4_truncated",
-    "diffusion_matrix", "hyperdiffusion_matrix", "ch_matrix",
-    "apply_tri", "apply_penta", "bands_to_dense",
+    "d2_dirichlet", "d2_noflux", "d2_periodic", "square_tridiag", "d4_truncated",
+    "diffusion_matrix", "diffusion_matrix_periodic", "hyperdiffusion_matrix", "ch_matrix",
+    "apply_tri", "apply_tri_periodic", "apply_penta", "bands_to_dense",
 ]
 
 
@@ -102,6 +105,21 @@ def d4_truncated(N):
     return a, b, c, d, e
 
 
+def d2_periodic(N):
+    """Periodic second difference: rows (1, -2, 1) everywhere, wrapping around;
+    sub[0] and sup[N-1] are the corner entries (section 3.3's matrix).  N >= 3."""
+    if N < 3:
+        raise ValueError("the periodic operator needs N >= 3")
+    return np.ones(N), -2.0 * np.ones(N), np.ones(N)
+
+
+def diffusion_matrix_periodic(N, r):
+    """A = I + r K with K = -D2_P: section 3.2's left-hand side with a = c = -r,
+    b = 1 + 2r on every row, the corners included.  Returns (a, b, c)."""
+    sub, dia, sup = d2_periodic(N)
+    return -r * sub, 1.0 - r * dia, -r * sup
+
+
 def diffusion_matrix(N, r):
     """A = I + r K with K = -D2_D = tridiag(-1, 2, -1): the backward-Euler matrix of
     the diffusion equation (section 3.2's coefficients a = c = -sigma,
@@ -140,6 +158,17 @@ def apply_tri(sub, dia, sup, x):
     if N > 1:
         y[1:] += sub[1:, None] * x[:-1]
         y[:-1] += sup[:-1, None] * x[1:]
+    return y
+
+
+def apply_tri_periodic(sub, dia, sup, x):
+    """y = T x for a periodic tridiagonal T (corners sub[0] at (0, N-1) and
+    sup[N-1] at (N-1, 0)), x of shape (N, M)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = apply_tri(sub, dia, sup, x)
+    N = x.shape[0]
+    y[0] += sub[0] * x[N - 1]
+    y[N - 1] += sup[N - 1] * x[0]
     return y
 
 

@@ -15,7 +15,8 @@ from . import banded, matrices
 
 __all__ = [
     "SharedTri", "SharedPenta",
-    "diffusion_be_step", "diffusion_cn_rhs", "hyper_be_step", "hyper_cn_rhs",
+    "SharedTriPeriodic", "diffusion_be_step", "diffusion_cn_rhs", "diffusion_cn_rhs_periodic",
+    "hyper_be_step", "hyper_cn_rhs",
     "ch_rhs", "ch_step", "solve_fp32_rhs",
 ]
 
@@ -35,6 +36,25 @@ class SharedTri:
 
     def apply(self, x):
         return matrices.apply_tri(self.a, self.b, self.c, x)
+
+
+class SharedTriPeriodic:
+    """A shared periodic tridiagonal matrix (section 3.3): A' factorised once and
+    z = A'^{-1} u solved once; every solve is a tridiagonal solve plus the
+    Sherman-Morrison correction."""
+
+    def __init__(self, a, b, c):
+        self.a, self.b, self.c = (np.asarray(v, dtype=np.float64) for v in (a, b, c))
+        self.fac = banded.tri_periodic_factor(self.a, self.b, self.c)
+
+    def solve(self, d):
+        return banded.tri_periodic_solve(self.fac, d)
+
+    def solve_adjoint(self, g):
+        return banded.tri_periodic_solve_adjoint(self.fac, g)
+
+    def apply(self, x):
+        return matrices.apply_tri_periodic(self.a, self.b, self.c, x)
 
 
 class SharedPenta:
@@ -64,6 +84,13 @@ def diffusion_cn_rhs(N, sigma, C):
     sigma C_{i-1} + (1 - 2 sigma) C_i + sigma C_{i+1} = (I - sigma K) C."""
     sub, dia, sup = matrices.d2_dirichlet(N)
     return np.asarray(C, dtype=np.float64) + sigma * matrices.apply_tri(sub, dia, sup, C)
+
+
+def diffusion_cn_rhs_periodic(N, sigma, C):
+    """Crank-Nicolson right-hand side of section 3.2's periodic scheme:
+    sigma C_{i-1} + (1 - 2 sigma) C_i + sigma C_{i+1} with the indices wrapping."""
+    sub, dia, sup = matrices.d2_periodic(N)
+    return np.asarray(C, dtype=np.float64) + sigma * matrices.apply_tri_periodic(sub, dia, sup, C)
 
 
 def hyper_be_step(A: SharedPenta, C):

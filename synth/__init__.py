@@ -33,6 +33,7 @@ __all__ = [
     "random_penta_diagonals",
     "sine_mode_block",
     "cosine_mode_block",
+    "fourier_mode_block",
     "torch_uniform",
     "torch_normal",
 ]
@@ -137,6 +138,16 @@ def cosine_mode_block(N: int, modes, amplitude: float = 1.0) -> np.ndarray:
     k = np.asarray(modes, dtype=np.int64)[None, :]
     phase = (k * (2 * i + 1)) % (4 * N)
     return amplitude * np.cos(phase.astype(np.float64) * np.pi / (2 * N))
+
+
+def fourier_mode_block(N: int, modes, kind: str = "cos") -> np.ndarray:
+    """Columns are the periodic grid modes cos(2 pi k i / N) (or sin), i = 0..N-1,
+    one column per k in ``modes``.  Shape ``(N, len(modes))``."""
+    # the integer phase k i is reduced modulo N exactly before scaling
+    i = np.arange(N, dtype=np.int64)[:, None]
+    k = np.asarray(modes, dtype=np.int64)[None, :]
+    phase = ((i * k) % N).astype(np.float64) * (2.0 * np.pi / N)
+    return np.cos(phase) if kind == "cos" else np.sin(phase)
 
 
 # --- device-side generators for the full-size workloads (torch Philox stream) ---
