@@ -84,6 +84,27 @@ int sb_factor_shared_tri(int64_t N, const double* a, const double* b, const doub
                          sb_factor** out);
 
 /*
+ * sb_factor_shared_tri_periodic -- factorise a shared periodic tridiagonal matrix
+ * (section 3.3): row i is a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] with the indices
+ * taken modulo N, so a[0] multiplies x[N-1] and c[N-1] multiplies x[0] (the corner
+ * entries).  As in section 3.3, A = A' + u v^T with u = (-b[0], 0, .., c[N-1]),
+ * v = (1, 0, .., -a[0]/b[0]); A' (no corners, b'[0] = 2 b[0], b'[N-1] = b[N-1] +
+ * a[0] c[N-1]/b[0]) is factored as by sb_factor_shared_tri and A'^{-1} u is solved
+ * once, in FP64 on the host.  Every solve with the handle (sb_solve_batched, _ex,
+ * _adjoint, _host, any dtype and arithmetic) returns x = y - f z with y = A'^{-1} b,
+ * z = A'^{-1} u and f = (v . y)/(1 + v . z), in one pass over the batch: y_0 is
+ * accumulated during the forward sweep and the correction is applied as x is
+ * written.  The transpose uses A^T = A'^T + v u^T the same way (no counterpart in
+ * the paper).  Refinement and group solves reject periodic handles
+ * (SB_ERR_UNSUPPORTED); the partitioned algorithm falls back to the sweeps.
+ *   N        >= 3.
+ *   a, b, c  host arrays of N doubles, all entries used.
+ * SB_ERR_SINGULAR for b[0] = 0, a zero pivot of A' or 1 + v . z = 0.
+ */
+int sb_factor_shared_tri_periodic(int64_t N, const double* a, const double* b, const double* c,
+                                  sb_factor** out);
+
+/*
  * sb_factor_shared_penta -- factorise a shared pentadiagonal matrix A = L R
  * (section 4.1; Algorithm 3 read with the section's equations).
  *
@@ -223,15 +244,20 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
  *                               D2N = rows (-1, 1), (1, -2, 1), ..., (1, -1): the
  *                               implicit matrix of section 5.1 with no-flux ends
  *                               (coef = dt * gamma in grid units).
- * `diags` is a host array of (2P+1)*N doubles (P = 1 for the diffusion matrix, 2
+ *   SB_MAT_DIFFUSION_PERIODIC   K = tridiag(-1, 2, -1) wrapping around (section 3.3's
+ *                               matrix; N >= 3): a[0] and c[N-1] are the corner
+ *                               entries; factor it with sb_factor_shared_tri_periodic.
+ * `diags` is a host array of (2P+1)*N doubles (P = 1 for the diffusion matrices, 2
  * otherwise), diagonal-major: diags[k*N + i] is row i of the diagonal at offset
- * k - P; entries outside the matrix are written as 0.  Host only; no GPU needed.
+ * k - P; entries outside the matrix are written as 0 (except the periodic
+ * corners).  Host only; no GPU needed.
  * Returns SB_ERR_INVALID_ARG for an unknown kind, N < 1, a NULL or non-finite input.
  */
 #define SB_MAT_DIFFUSION_DIRICHLET 1
 #define SB_MAT_HYPER_HINGED        2
 #define SB_MAT_HYPER_TRUNCATED     3
 #define SB_MAT_CH_NOFLUX           4
+#define SB_MAT_DIFFUSION_PERIODIC  5
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
 
 /*

@@ -31,7 +31,8 @@ SB_MAT_DIFFUSION_DIRICHLET = 1
 SB_MAT_HYPER_HINGED = 2
 SB_MAT_HYPER_TRUNCATED = 3
 SB_MAT_CH_NOFLUX = 4
-MATRIX_KINDS = {"diffusion": 1, "hinged": 2, "truncated": 3, "ch_noflux": 4}
+SB_MAT_DIFFUSION_PERIODIC = 5
+MATRIX_KINDS = {"diffusion": 1, "hinged": 2, "truncated": 3, "ch_noflux": 4, "diffusion_periodic": 5}
 
 _ERR_NAMES = {
     SB_ERR_INVALID_ARG: "SB_ERR_INVALID_ARG",
@@ -59,6 +60,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 # name -> (restype, argtypes); the full exported surface of include/sbsolve.h
 SIGNATURES = {
     "sb_factor_shared_tri": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
+    "sb_factor_shared_tri_periodic": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
     "sb_factor_shared_penta": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
     "sb_factor_destroy": (None, [_vp]),
     "sb_factor_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_c_i64)]),
@@ -204,6 +206,18 @@ def sb_factor_shared_tri(a, b, c) -> Factor:
     return Factor(h.value, 1, N, arrs)
 
 
+def sb_factor_shared_tri_periodic(a, b, c) -> Factor:
+    """Factorise a shared periodic tridiagonal matrix (section 3.3): a[0] and c[N-1]
+    are the corner entries.  Solves with the handle apply the Sherman-Morrison
+    correction."""
+    N = len(b)
+    arrs = [_host_f64(v, N) for v in (a, b, c)]
+    h = ctypes.c_void_p()
+    _check(lib().sb_factor_shared_tri_periodic(N, *[x.ctypes.data_as(_dp) for x in arrs],
+                                               ctypes.byref(h)))
+    return Factor(h.value, 1, N, arrs)
+
+
 def sb_factor_shared_penta(a, b, c, d, e) -> Factor:
     """Factorise the shared pentadiagonal matrix (offsets -2..+2) once."""
     N = len(c)
@@ -299,7 +313,7 @@ def sb_build_matrix(kind, N: int, coef: float):
     """Diagonals of a workload matrix I + coef*K (see include/sbsolve.h) as a
     tuple of 3 (tridiagonal) or 5 (pentadiagonal) NumPy arrays, offsets -P..P."""
     code = MATRIX_KINDS[kind] if isinstance(kind, str) else int(kind)
-    P = 1 if code == SB_MAT_DIFFUSION_DIRICHLET else 2
+    P = 1 if code in (SB_MAT_DIFFUSION_DIRICHLET, SB_MAT_DIFFUSION_PERIODIC) else 2
     out = np.zeros((2 * P + 1) * N, dtype=np.float64)
     _check(lib().sb_build_matrix(code, N, float(coef), out.ctypes.data_as(_dp)))
     return tuple(out.reshape(2 * P + 1, N))

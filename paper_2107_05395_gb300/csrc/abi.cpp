@@ -246,7 +246,7 @@ static int upload_factor(sb_factor* f) {
   SB_CUDA(cudaMemcpy(f->arowdf, arowdf.data(), arowdf.size() * sizeof(float), cudaMemcpyHostToDevice));
   // images of the partitioned solve of A and A^T (FP32) for each variant: chunks of
   // the shortest L that covers N (16/32/64 rows for 16 chunks, 8/16/32 for 32), N >= 64
-  for (int v = 0; v < kPartVariants; ++v) {
+  for (int v = 0; v < kPartVariants && !f->periodic; ++v) {
     const int P = part_chunks(v);
     int L = 0;
     const int lens[3] = {v == 0 ? 16 : 8, v == 0 ? 32 : 16, v == 0 ? 64 : 32};
@@ -278,7 +278,7 @@ static int upload_factor(sb_factor* f) {
     int L64 = 0;
     for (int cand : {8, 16, 32})
       if (L64 == 0 && (int64_t)cand * kPart64Chunks >= N) L64 = cand;
-    if (N >= 32 && L64 > 0) {
+    if (N >= 32 && L64 > 0 && !f->periodic) {
       for (int o = 0; o < 2; ++o) {
         std::vector<double> dt;
         const double* d = f->h_diag.data();
@@ -309,6 +309,7 @@ static void free_factor(sb_factor* f) {
     if (f->diag64) cudaFree(f->diag64);
     if (f->arow64) cudaFree(f->arow64);
     if (f->arowdf) cudaFree(f->arowdf);
+    if (f->cyc64) cudaFree(f->cyc64);
     for (auto& per_op : f->part_img)
       for (float* p : per_op)
         if (p) cudaFree(p);
@@ -318,7 +319,8 @@ static void free_factor(sb_factor* f) {
   delete f;
 }
 
-static int make_factor(int P, int64_t N, const double* const* diags, sb_factor** out) {
+static int make_factor(int P, int64_t N, const double* const* diags, sb_factor** out,
+                       bool periodic = false) {
   if (out == nullptr) return fail(SB_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (N < 1) return fail(SB_ERR_INVALID_ARG, "N must be >= 1 (got %lld)", (long long)N);
@@ -335,6 +337,7 @@ static int make_factor(int P, int64_t N, const double* const* diags, sb_factor**
   if (!f) return fail(SB_ERR_ALLOC, "host allocation failed");
   f->P = P;
   f->N = N;
+  f->periodic = periodic;
   int rc = (P == 1) ? factor_tri_host(N, diags[0], diags[1], diags[2], f->h_coef)
                     : factor_penta_host(N, diags[0], diags[1], diags[2], diags[3], diags[4],
                                         f->h_coef);
@@ -402,6 +405,12 @@ int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, i
         diags[N + i] = 1.0 + 2.0 * coef;
         diags[2 * N + i] = (i + 1 < N) ? -coef : 0.0;
       }
+      return SB_OK;
+    case SB_MAT_DIFFUSION_PERIODIC:
+      if (N < 3) return fail(SB_ERR_INVALID_ARG, "the periodic matrix needs N >= 3");
+      *P = 1;
+      diags.assign(3 * N, -coef);  // the corners a[0], c[N-1] included
+      for (int64_t i = 0; i < N; ++i) diags[N + i] = 1.0 + 2.0 * coef;
       return SB_OK;
     case SB_MAT_HYPER_HINGED:
       square_tridiagonal(N, lo, mid, up, K);
@@ -481,6 +490,111 @@ int sb_factor_shared_tri(int64_t N, const double* a, const double* b, const doub
   clear_error();
   const double* d[3] = {a, b, c};
   return make_factor(1, N, d, out);
+}
+
+// Plain Thomas solve of the tridiagonal (a, b, c) (a[0], c[N-1] unused), or of its
+// transpose, for the periodic correction vectors (host, FP64, once per factor).
+static bool thomas_host(const std::vector<double>& a, const std::vector<double>& b,
+                        const std::vector<double>& c, std::vector<double> r, bool transpose,
+                        std::vector<double>& x) {
+  const int64_t N = (int64_t)b.size();
+  std::vector<double> lo(N, 0.0), up(N, 0.0);  // sub- and super-diagonal of the solved matrix
+  for (int64_t i = 0; i < N; ++i) {
+    lo[i] = transpose ? (i > 0 ? c[i - 1] : 0.0) : (i > 0 ? a[i] : 0.0);
+    up[i] = transpose ? (i + 1 < N ? a[i + 1] : 0.0) : (i + 1 < N ? c[i] : 0.0);
+  }
+  std::vector<double> cp(N, 0.0);
+  for (int64_t i = 0; i < N; ++i) {
+    const double piv = b[i] - (i > 0 ? lo[i] * cp[i - 1] : 0.0);
+    if (piv == 0.0 || !std::isfinite(piv)) return false;
+    cp[i] = up[i] / piv;
+    r[i] = (r[i] - (i > 0 ? lo[i] * r[i - 1] : 0.0)) / piv;
+  }
+  x.assign(N, 0.0);
+  for (int64_t i = N - 1; i >= 0; --i) x[i] = r[i] - (i + 1 < N ? cp[i] * x[i + 1] : 0.0);
+  return true;
+}
+
+int sb_factor_shared_tri_periodic(int64_t N, const double* a, const double* b, const double* c,
+                                  sb_factor** out) {
+  clear_error();
+  if (out == nullptr) return fail(SB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 3) return fail(SB_ERR_INVALID_ARG, "a periodic tridiagonal matrix needs N >= 3 (got %lld)",
+                         (long long)N);
+  if (!a || !b || !c) return fail(SB_ERR_INVALID_ARG, "a diagonal is NULL");
+  if (!finite_all(a, 0, N) || !finite_all(b, 0, N) || !finite_all(c, 0, N))
+    return fail(SB_ERR_INVALID_ARG, "a diagonal has a non-finite entry");
+  if (b[0] == 0.0) return fail(SB_ERR_SINGULAR, "b[0] = 0: the rank-one split of section 3.3 needs b[0] != 0");
+  // A = A' + u v^T, u = (-b_0, 0.., c_{N-1}), v = (1, 0.., -a_0/b_0)  (section 3.3)
+  std::vector<double> ap(a, a + N), bp(b, b + N), cp(c, c + N), u(N, 0.0), v(N, 0.0);
+  u[0] = -b[0];
+  u[N - 1] = c[N - 1];
+  v[0] = 1.0;
+  v[N - 1] = -a[0] / b[0];
+  ap[0] = 0.0;
+  cp[N - 1] = 0.0;
+  bp[0] = b[0] - u[0] * v[0];
+  bp[N - 1] = b[N - 1] - u[N - 1] * v[N - 1];
+  const double* d[3] = {ap.data(), bp.data(), cp.data()};
+  sb_factor* f = nullptr;
+  SB_TRY(make_factor(1, N, d, &f, true));
+  // correction data, per op: rows (w_i, -z_i), alpha, beta (see sb_factor)
+  std::vector<double> e0(N, 0.0), z, w, zt, wt;
+  e0[0] = 1.0;
+  bool ok = thomas_host(ap, bp, cp, u, false, z) && thomas_host(ap, bp, cp, e0, true, w) &&
+            thomas_host(ap, bp, cp, v, true, zt) && thomas_host(ap, bp, cp, e0, false, wt);
+  double vz = 0.0, uzt = 0.0;
+  for (int64_t i = 0; ok && i < N; ++i) {
+    vz += v[i] * z[i];
+    uzt += u[i] * zt[i];
+  }
+  if (!ok || 1.0 + vz == 0.0 || 1.0 + uzt == 0.0 || !std::isfinite(vz) || !std::isfinite(uzt)) {
+    sb_factor_destroy(f);
+    return fail(SB_ERR_SINGULAR, "the periodic matrix is singular (1 + v.A'^{-1}u = 0)");
+  }
+  // primal: f = (v.y)/(1 + v.z), v.y = y_0 + v_{N-1} y_{N-1}
+  f->cyc_alpha[0] = v[N - 1];
+  f->cyc_beta[0] = 1.0 / (1.0 + vz);
+  // adjoint: f = (u.y)/(1 + u.z'), u.y = u_0 (y_0 + (u_{N-1}/u_0) y_{N-1})
+  f->cyc_alpha[1] = u[N - 1] / u[0];
+  f->cyc_beta[1] = u[0] / (1.0 + uzt);
+  std::vector<double> h(4 * N);
+  for (int64_t i = 0; i < N; ++i) {
+    h[2 * i] = w[i];
+    h[2 * i + 1] = -z[i];
+    h[2 * N + 2 * i] = wt[i];
+    h[2 * N + 2 * i + 1] = -zt[i];
+  }
+  std::vector<float> h32(4 * N), hdf(8 * N);
+  for (int64_t k = 0; k < 4 * N; ++k) {
+    h32[k] = (float)h[k];
+    hdf[2 * k] = (float)h[k];
+    hdf[2 * k + 1] = (float)(h[k] - (double)hdf[2 * k]);
+  }
+  int rc = SB_OK;
+  {
+    DeviceGuard g(f->device);
+    rc = g.rc;
+    void* mem = nullptr;
+    if (rc == SB_OK) rc = cuda_check(cudaMalloc(&mem, 4 * N * 8 + 4 * N * 4 + 8 * N * 4), "cudaMalloc");
+    if (rc == SB_OK) {
+      f->cyc64 = static_cast<double*>(mem);
+      f->cyc32 = reinterpret_cast<float*>(f->cyc64 + 4 * N);
+      f->cycdf = f->cyc32 + 4 * N;
+      rc = cuda_check(cudaMemcpy(f->cyc64, h.data(), 4 * N * 8, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+    if (rc == SB_OK)
+      rc = cuda_check(cudaMemcpy(f->cyc32, h32.data(), 4 * N * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (rc == SB_OK)
+      rc = cuda_check(cudaMemcpy(f->cycdf, hdf.data(), 8 * N * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  }
+  if (rc != SB_OK) {
+    sb_factor_destroy(f);
+    return rc;
+  }
+  *out = f;
+  return SB_OK;
 }
 
 int sb_factor_shared_penta(int64_t N, const double* a, const double* b, const double* c,

@@ -369,6 +369,8 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
   std::vector<int64_t> Ms, lds;
   for (int g = 0; g < G; ++g) {
     if (!fs[g]) return fail(SB_ERR_INVALID_ARG, "factor %d is NULL", g);
+    if (fs[g]->periodic)
+      return fail(SB_ERR_UNSUPPORTED, "factor %d is periodic: use sb_solve_batched_ex", g);
     if (fs[g]->P != fs[0]->P)
       return fail(SB_ERR_UNSUPPORTED, "all groups of one call must have the same bandwidth");
     if (fs[g]->device != fs[0]->device)
@@ -585,6 +587,7 @@ extern "C" int sb_solve_batched_refined_noalloc(const sb_factor* f, const float*
                                                 sb_arith residual_arith, void* stream) {
   clear_error();
   if (f == nullptr) return fail(SB_ERR_INVALID_ARG, "factor handle is NULL");
+  if (f->periodic) return fail(SB_ERR_UNSUPPORTED, "periodic factors are not refined: use sb_solve_batched_ex");
   if (M < 0 || ld < M || ld < 1)
     return fail(SB_ERR_INVALID_ARG, "need M >= 0 and ld >= max(M, 1)");
   if (n_refine < 0 || n_refine > 16) return fail(SB_ERR_INVALID_ARG, "n_refine must be in [0, 16]");

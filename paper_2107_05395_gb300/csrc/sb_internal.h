@@ -89,7 +89,16 @@ struct sb_factor {
   int part64_L = 0;
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
-  std::vector<double> h_diag;  // host copy of diag64
+  std::vector<double> h_diag;  // host copy of diag64 (of A' for a periodic factor)
+  // Periodic tridiagonal (section 3.3): the factors above are those of A' and each
+  // solve applies the Sherman-Morrison correction x = y - f z with
+  // f = beta (y_0 + alpha y_{N-1}) and y_0 = w . rhs accumulated in the forward
+  // sweep.  Per op (A, A^T): rows (w_i, -z_i) on the device, alpha and beta on the host.
+  bool periodic = false;
+  double* cyc64 = nullptr;  // device: [op][N][2], FP64
+  float* cyc32 = nullptr;   // device: the same rounded to FP32
+  float* cycdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
+  double cyc_alpha[2] = {0.0, 0.0}, cyc_beta[2] = {0.0, 0.0};
 };
 
 struct sb_stepper {

@@ -24,34 +24,66 @@ namespace sb {
 namespace {
 
 // Single-factor kernel: persistent CTAs stage the coefficients once, then their
-// warps take tiles round-robin over the grid.
-template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
+// warps take tiles round-robin over the grid.  CYC: the periodic tridiagonal
+// matrix (section 3.3); its correction rows are staged after the coefficients.
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
+          bool CYC>
 __global__ void __launch_bounds__(512)
 sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld,
-             const TI* rhs, TO* x, int64_t ntiles) {
+             const TI* rhs, TO* x, int64_t ntiles, const typename A::C* __restrict__ cyc,
+             typename A::C alpha, typename A::C beta) {
   using C = typename A::C;
   constexpr int W = P + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cs = reinterpret_cast<C*>(smem_raw);
   stage(cs, coef, 2 * W * N);
+  if constexpr (CYC) stage(cs + 2 * W * N, cyc, 2 * N);
   __syncthreads();
   const int nw = blockDim.x >> 5;
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
        tile += (int64_t)gridDim.x * nw)
-    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R>(cs, cs + W * N, N, M, ld, rhs, x, tile);
+    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC>(cs, cs + W * N, N, M, ld, rhs, x, tile,
+                                                         cs + 2 * W * N, alpha, beta);
 }
+
+// The periodic correction data of a factor for an arithmetic policy: (w_i, -z_i)
+// rows of op `o` and the scalars alpha, beta as coefficients.
+template <class A>
+struct CycData;
+template <>
+struct CycData<NativeArith<double>> {
+  static const double* rows(const sb_factor* f, int o) { return f->cyc64 ? f->cyc64 + 2 * f->N * o : nullptr; }
+  static double coef(double v) { return v; }
+};
+template <>
+struct CycData<NativeArith<float>> {
+  static const float* rows(const sb_factor* f, int o) { return f->cyc32 ? f->cyc32 + 2 * f->N * o : nullptr; }
+  static float coef(double v) { return (float)v; }
+};
+template <>
+struct CycData<DFArith> {
+  static const df* rows(const sb_factor* f, int o) {
+    return f->cycdf ? reinterpret_cast<const df*>(f->cycdf) + 2 * f->N * o : nullptr;
+  }
+  static df coef(double v) {
+    const float h = (float)v;
+    return df{h, (float)(v - (double)h)};
+  }
+};
 
 // ----------------------------------------------------------------- launching
 
-template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
+          bool CYC>
 int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
-           int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+           int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
+  using C = typename A::C;
   const int N = (int)f->N;
-  const size_t smem = (size_t)2 * (P + 1) * N * sizeof(typename A::C);
+  const size_t smem = ((size_t)2 * (P + 1) * N + (CYC ? (size_t)2 * N : 0)) * sizeof(C);
   if (smem > 227 * 1024)
     return fail(SB_ERR_UNSUPPORTED,
                 "N=%d: the shared factors (%zu B) exceed the shared memory of one CTA", N, smem);
-  auto k = sweep_kernel<A, P, F_ONE, B_ONE, TI, TO, SPT, R>;
+  auto k = sweep_kernel<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC>;
   const int threads = shape.threads;
   if (threads < 32 || threads > 512 || threads % 32 != 0)
     return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, 512]");
@@ -63,31 +95,40 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   // (tile = block + grid * warp) so that every SM gets an equal share
   const int64_t grid =
       std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
+  const C* cyc = CYC ? CycData<A>::rows(f, op) : nullptr;
+  const C alpha = CycData<A>::coef(CYC ? f->cyc_alpha[op] : 0.0);
+  const C beta = CycData<A>::coef(CYC ? f->cyc_beta[op] : 0.0);
   k<<<(unsigned)grid, threads, smem, stream>>>(coef, N, M, ld, static_cast<const TI*>(rhs),
-                                              static_cast<TO*>(x), ntiles);
+                                              static_cast<TO*>(x), ntiles, cyc, alpha, beta);
   return cuda_check(cudaGetLastError(), "sweep kernel launch");
 }
 
-template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO>
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, bool CYC>
 int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
-               int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+               int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
   if (shape.spt == 2)
-    return launch<A, P, F_ONE, B_ONE, TI, TO, 2, 4>(f, coef, rhs, x, M, ld, shape, stream);
+    return launch<A, P, F_ONE, B_ONE, TI, TO, 2, 4, CYC>(f, coef, rhs, x, M, ld, shape, stream, op);
   if (shape.spt != 1) return fail(SB_ERR_INVALID_ARG, "systems per thread must be 1 or 2");
-  return launch<A, P, F_ONE, B_ONE, TI, TO, 1, kRows>(f, coef, rhs, x, M, ld, shape, stream);
+  return launch<A, P, F_ONE, B_ONE, TI, TO, 1, kRows, CYC>(f, coef, rhs, x, M, ld, shape, stream, op);
 }
 
 template <class A, typename TI, typename TO>
 int dispatch_pb(const sb_factor* f, Op op, const typename A::C* base, const void* rhs, void* x,
                 int64_t M, int64_t ld, const SweepShape& shape, cudaStream_t stream) {
   const typename A::C* c = base + (op == OP_PRIMAL ? 0 : op_block_len(f->P, f->N));
-  if (f->P == 1)
+  const int o = op == OP_PRIMAL ? 0 : 1;
+  if (f->P == 1) {
+    if (f->periodic)
+      return op == OP_PRIMAL
+                 ? launch_spt<A, 1, false, true, TI, TO, true>(f, c, rhs, x, M, ld, shape, stream, o)
+                 : launch_spt<A, 1, true, false, TI, TO, true>(f, c, rhs, x, M, ld, shape, stream, o);
     return op == OP_PRIMAL
-               ? launch_spt<A, 1, false, true, TI, TO>(f, c, rhs, x, M, ld, shape, stream)
-               : launch_spt<A, 1, true, false, TI, TO>(f, c, rhs, x, M, ld, shape, stream);
+               ? launch_spt<A, 1, false, true, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o)
+               : launch_spt<A, 1, true, false, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o);
+  }
   return op == OP_PRIMAL
-             ? launch_spt<A, 2, false, true, TI, TO>(f, c, rhs, x, M, ld, shape, stream)
-             : launch_spt<A, 2, true, false, TI, TO>(f, c, rhs, x, M, ld, shape, stream);
+             ? launch_spt<A, 2, false, true, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o)
+             : launch_spt<A, 2, true, false, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o);
 }
 
 }  // namespace

@@ -43,15 +43,21 @@ __device__ __forceinline__ void stage(C* dst, const C* __restrict__ src, int n) 
 }
 
 // Solves the tile `tile` (32 * SPT consecutive systems) with coefficient rows
-// fw (forward) and bw (backward):
+// fw (forward) and bw (backward) (with CYC, the periodic matrix of section 3.3:
+// rows cy = (w_i, -z_i) and scalars alpha, beta give the Sherman-Morrison
+// correction x = y - f z, f = beta (w . rhs + alpha y_{N-1}), applied as x is
+// written):
 //   forward  u_i = F0 r_i - F1 u_{i-1} - F2 u_{i-2}      (F0 == 1 when F_ONE)
 //   backward x_i = B0 u_i - B1 x_{i+1} - B2 x_{i+2}      (B0 == 1 when B_ONE)
 // The intermediate u is stored in place in x; SPT systems per thread (m and
 // m + 32, ...) interleave independent recurrences; R rows per prefetch batch.
-template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R>
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
+          bool CYC = false>
 __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typename A::C* bw, int N,
                                            int64_t M, int64_t ld, const TI* rhs, TO* x,
-                                           int64_t tile) {
+                                           int64_t tile, const typename A::C* cy = nullptr,
+                                           typename A::C alpha = typename A::C(),
+                                           typename A::C beta = typename A::C()) {
   using V = typename A::V;
   using C = typename A::C;
   using S = typename A::S;
@@ -71,9 +77,9 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
     };
 
     // ---- forward sweep
-    V u1[SPT], u2[SPT];
+    V u1[SPT], u2[SPT], dot[SPT];
 #pragma unroll
-    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = A::zero();
+    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = dot[s] = A::zero();
     TI va[R][SPT], vb[R][SPT];
     auto load_in = [&](TI (&buf)[R][SPT], int i0) {
 #pragma unroll
@@ -90,7 +96,9 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
           const C* c = fw + W * i;
 #pragma unroll
           for (int s = 0; s < SPT; ++s) {
-            const V u = A::template step<P, F_ONE>(c, Conv<A, TI>::in(buf[j][s]), u1[s], u2[s]);
+            const V in = Conv<A, TI>::in(buf[j][s]);
+            const V u = A::template step<P, F_ONE>(c, in, u1[s], u2[s]);
+            if constexpr (CYC) dot[s] = A::fmac(cy[2 * i], in, dot[s]);
             if (ok[s]) *slot(i, s) = A::to_store(u);
             u2[s] = u1[s];
             u1[s] = u;
@@ -107,9 +115,9 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
     }
 
     // ---- backward sweep
-    V x1[SPT], x2[SPT];
+    V x1[SPT], x2[SPT], fc[SPT];
 #pragma unroll
-    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = A::zero();
+    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = fc[s] = A::zero();
     S sa[R][SPT], sb_[R][SPT];
     auto load_mid = [&](S (&buf)[R][SPT], int i0) {
 #pragma unroll
@@ -127,7 +135,12 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
 #pragma unroll
           for (int s = 0; s < SPT; ++s) {
             const V xi = A::template step<P, B_ONE>(c, A::from_store(buf[j][s]), x1[s], x2[s]);
-            if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(xi));
+            if constexpr (CYC) {
+              if (i == N - 1) fc[s] = A::mulc(beta, A::fmac(alpha, xi, dot[s]));
+              if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(A::fmac(cy[2 * i + 1], fc[s], xi)));
+            } else {
+              if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(xi));
+            }
             x2[s] = x1[s];
             x1[s] = xi;
           }

@@ -120,6 +120,19 @@ def test_product_matrix_builder_matches_oracle(sb, kind, N):
         assert np.all(u[[i for i in range(N) if i not in rows]] == 0.0)
 
 
+@pytest.mark.parametrize("N", [3, 4, 17, 256])
+def test_product_periodic_matrix_builder_matches_oracle(sb, N):
+    """The periodic diffusion matrix: all three diagonals equal the oracle's,
+    corners included (a[0] couples x[N-1], c[N-1] couples x[0])."""
+    from oracle import matrices
+    mine = sb.sb_build_matrix("diffusion_periodic", N, 0.37)
+    ref = matrices.diffusion_matrix_periodic(N, 0.37)
+    for u, v in zip(mine, ref):
+        assert np.allclose(u, v, rtol=0, atol=1e-15)
+    with pytest.raises(sb.SbError):
+        sb.sb_build_matrix("diffusion_periodic", 2, 0.37)
+
+
 def test_product_matrix_builder_rejects_bad_input(sb):
     with pytest.raises(sb.SbError):
         sb.sb_build_matrix(99, 8, 0.1)
