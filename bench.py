@@ -323,6 +323,28 @@ def extra_cahn_hilliard(sb, torch, stream):
     return out
 
 
+def extra_periodic_cn(sb, torch, stream):
+    """The paper's own tridiagonal benchmark (Table 1): 1000 Crank-Nicolson steps of
+    1D periodic diffusion (sections 3.2-3.3), M = 2^16 systems, N = 64, 256, 1024,
+    here in FP64 with the right-hand side built inside the fused step and the
+    Sherman-Morrison correction inside the sweep, 64-step CUDA graphs.  The paper's
+    V100 seconds (which include its separate stencil kernel) are quoted as context."""
+    import synth
+    paper_v100_s = {64: 1.278, 256: 5.015, 1024: 20.268}  # Table 1, M = 2^16 rows
+    M, steps, sigma = 1 << 16, 1000, 0.5
+    out = {"workload": "periodic CN diffusion, M=2^16, 1000 steps, sigma=0.5, U[-1,1], FP64"}
+    for N in (64, 256, 1024):
+        st = sb.sb_stepper_create("diffusion", "cn", "periodic", N, sigma, 0.0)
+        C = synth.torch_uniform(11, N, M, -1.0, 1.0, torch.float64, "cuda")
+        sb.sb_stepper_run(st, C, 64)  # builds the graph
+        ms = _events_ms(lambda: sb.sb_stepper_run(st, C, steps), 1, torch.cuda.current_stream())
+        out[f"N{N}"] = {"s_per_1000_steps": ms * 1e-3 * 1000 / steps, "ms_per_step": ms / steps,
+                        "algorithmic_gbs": 16.0 * N * M / (ms / steps * 1e-3) / 1e9,
+                        "paper_v100_s_per_1000_steps": paper_v100_s[N]}
+        del C
+    return out
+
+
 def extra_rollout(sb, torch, stream):
     """Adjoint rollout, N=512, 2^16 systems, 200 steps, checkpoints every 20 (CH
     and diffusion, FP64): forward and backward step rates against the plain
@@ -484,7 +506,8 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         for name, fn in (("tri_latency", extra_tri_latency), ("multigroup_refine", extra_multigroup),
-                         ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout)):
+                         ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout),
+                         ("paper_table1_periodic_cn", extra_periodic_cn)):
             try:
                 extras[name] = fn(sb, torch, stream)
             except Exception as exc:  # report, do not hide, a failing extra

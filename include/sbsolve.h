@@ -348,7 +348,11 @@ int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const*
  *   SB_STEP_DIFFUSION      A = I + coef K, K = tridiag(-1, 2, -1) with Dirichlet rows.
  *                          SB_SCHEME_BE: B = I (backward Euler, coef = r = dt/dx^2);
  *                          SB_SCHEME_CN: B = I - coef K (section 3.2's Crank-Nicolson,
- *                          coef = sigma = dt/(2 dx^2)).  bc must be SB_BC_DIRICHLET.
+ *                          coef = sigma = dt/(2 dx^2)).  bc SB_BC_DIRICHLET, or
+ *                          SB_BC_PERIODIC (the paper's own ends, sections 3.2-3.3:
+ *                          K wraps around, A is factored as by
+ *                          sb_factor_shared_tri_periodic and every step applies the
+ *                          Sherman-Morrison correction inside the fused kernel).
  *   SB_STEP_HYPERDIFFUSION A = I + coef D4 with bc SB_BC_HINGED (D4 = D2 D2) or
  *                          SB_BC_TRUNCATED (Toeplitz 1,-4,6,-4,1); B = I (BE) or
  *                          I - coef D4 (section 4.2's Crank-Nicolson).
@@ -367,6 +371,7 @@ typedef struct sb_stepper sb_stepper;
 #define SB_BC_HINGED    1
 #define SB_BC_TRUNCATED 2
 #define SB_BC_NOFLUX    3
+#define SB_BC_PERIODIC  4
 /* run modes: fused step kernel replayed from a captured CUDA graph (64 steps per
  * graph; falls back to direct launches on the legacy NULL stream or while the
  * stream is being captured), fused kernel launched directly, or the unfused

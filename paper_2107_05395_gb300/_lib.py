@@ -394,7 +394,7 @@ def sb_solve_batched_groups(factors, rhs, x, arith="native", n_refine=0, residua
 
 STEP_KINDS = {"diffusion": 1, "hyperdiffusion": 2, "cahn_hilliard": 3}
 SCHEMES = {"be": 0, "cn": 1}
-BCS = {"dirichlet": 0, "hinged": 1, "truncated": 2, "noflux": 3}
+BCS = {"dirichlet": 0, "hinged": 1, "truncated": 2, "noflux": 3, "periodic": 4}
 RUN_MODES = {"graph": 0, "direct": 1, "unfused": 2}
 
 

@@ -293,6 +293,8 @@ int check_rollout(const sb_stepper* st, int64_t M, int64_t ld, int64_t T, int64_
   if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
   if (st->scheme != SB_SCHEME_BE)
     return fail(SB_ERR_UNSUPPORTED, "the rollout adjoint supports backward-Euler and Cahn-Hilliard steppers");
+  if (st->fac->periodic)
+    return fail(SB_ERR_UNSUPPORTED, "the rollout adjoint does not support periodic ends");
   if (M < 1 || ld < M) return fail(SB_ERR_INVALID_ARG, "need M >= 1 and ld >= M");
   if (T < 1 || k < 1) return fail(SB_ERR_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
   if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)

@@ -40,10 +40,14 @@ struct StConv<DFArith, double> {
 
 // rcoef rows: if NB > 0, NB values per row (B at offsets -(NB/2)..NB/2), then if
 // HAS_E, 3 values per row (E at offsets -1..1).  Out-of-matrix entries are 0.
-template <class A, int P, int NB, bool HAS_E, int R>
+// CYC: periodic ends (section 3.3): the window wraps (row -1 is row N-1, row N is
+// row 0) and the solve applies the Sherman-Morrison correction with the factor's
+// rows cyc = (w_i, -z_i) and scalars alpha, beta (see sweep_tile.cuh).
+template <class A, int P, int NB, bool HAS_E, int R, bool CYC>
 __global__ void __launch_bounds__(512)
 fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
-                  int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles) {
+                  int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles,
+                  const typename A::C* __restrict__ cyc, typename A::C alpha, typename A::C beta) {
   using V = typename A::V;
   using C = typename A::C;
   using S = typename A::S;
@@ -57,11 +61,14 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     const int n = 2 * W * N;
     for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
     for (int k = threadIdx.x; k < RW * N; k += blockDim.x) cs[n + k] = rcoef[k];
+    if constexpr (CYC)
+      for (int k = threadIdx.x; k < 2 * N; k += blockDim.x) cs[n + RW * N + k] = cyc[k];
   }
   __syncthreads();
   const C* fw = cs;
   const C* bw = cs + W * N;
   const C* rc = cs + 2 * W * N;
+  const C* cy = rc + RW * N;
 
   const int lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
@@ -95,7 +102,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         pw[2] = A::cubic(cw[3]);  // phi(C_{i+1}) once C_{i+1} entered the window
       }
     };
-    V u1 = A::zero(), u2 = A::zero();
+    V u1 = A::zero(), u2 = A::zero(), dot = A::zero();
     auto build_and_sweep = [&](int i) {
       V r;
       if constexpr (NB > 0) {
@@ -113,13 +120,23 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         r = A::fmac(e[2], pw[2], r);
       }
       const V u = A::template step<P, false>(fw + W * i, r, u1, u2);
+      if constexpr (CYC) dot = A::fmac(cy[2 * i], r, dot);
       *reinterpret_cast<S*>(y + (int64_t)i * ld) = A::to_store(u);
       u2 = u1;
       u1 = u;
     };
-    // prime: rows 0 and 1 enter the window before row 0 is built (rows -2, -1 are 0)
+    // prime: rows 0 and 1 enter the window before row 0 is built (rows -2, -1 are 0,
+    // or with periodic ends row -1 is row N-1; both wrapped rows are read before the
+    // forward sweep overwrites anything)
     load_rows(va, 0);
     load_rows(vb, R);
+    double c0 = 0.0;
+    if constexpr (CYC) {
+      c0 = va[0];
+      // three pushes (rows 0, 1, 2) precede the build of row 0 and each shifts the
+      // window left by one, so the last slot now ends up holding row -1
+      cw[4] = StConv<A, double>::in(c[(int64_t)(N - 1) * ld]);
+    }
     push(N > 0 ? va[0] : 0.0);
     push(N > 1 ? va[1] : 0.0);
     // row i needs raw row i + 2: from the current buffer or the next one
@@ -129,7 +146,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 + j;
         if (i < N) {
           const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R]) : 0.0;
+          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R]) : (CYC && i + 2 == N ? c0 : 0.0);
           push(v);
           build_and_sweep(i);
         }
@@ -140,7 +157,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 + R + j;
         if (i < N) {
           const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R]) : 0.0;
+          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R]) : (CYC && i + 2 == N ? c0 : 0.0);
           push(v);
           build_and_sweep(i);
         }
@@ -149,7 +166,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     }
 
     // backward sweep (B0 == 1 for the primal factors)
-    V x1 = A::zero(), x2 = A::zero();
+    V x1 = A::zero(), x2 = A::zero(), fc = A::zero();
     S sa[R], sb_[R];
     auto load_mid = [&](S (&buf)[R], int i0) {
 #pragma unroll
@@ -162,7 +179,12 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 - j;
         if (i >= 0) {
           const V xi = A::template step<P, true>(bw + W * i, A::from_store(buf[j]), x1, x2);
-          y[(int64_t)i * ld] = StConv<A, double>::out(xi);
+          if constexpr (CYC) {
+            if (i == N - 1) fc = A::mulc(beta, A::fmac(alpha, xi, dot));
+            y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[2 * i + 1], fc, xi));
+          } else {
+            y[(int64_t)i * ld] = StConv<A, double>::out(xi);
+          }
           x2 = x1;
           x1 = xi;
         }
@@ -178,8 +200,9 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
   }
 }
 
-// Unfused right-hand side (the paper's separate stencil pass): f = B C + E phi(C).
-template <class A, int NB, bool HAS_E>
+// Unfused right-hand side (the paper's separate stencil pass): f = B C + E phi(C);
+// CYC: periodic ends (row -1 is row N-1, row N is row 0).
+template <class A, int NB, bool HAS_E, bool CYC>
 __global__ void rhs_kernel(const typename A::C* __restrict__ rcoef, int N, int64_t M, int64_t ld,
                            const double* __restrict__ C_in, double* __restrict__ f) {
   using V = typename A::V;
@@ -189,6 +212,7 @@ __global__ void rhs_kernel(const typename A::C* __restrict__ rcoef, int N, int64
   const int i = blockIdx.y;
   if (m >= M || i >= N) return;
   auto val = [&](int k) -> V {
+    if constexpr (CYC) k = k < 0 ? k + N : (k >= N ? k - N : k);
     return (k >= 0 && k < N) ? StConv<A, double>::in(C_in[(int64_t)k * ld + m]) : A::zero();
   };
   const C* row = rcoef + RW * i;
@@ -220,16 +244,34 @@ namespace {
 constexpr int kStepRows = 8;
 constexpr int kGraphSteps = 64;  // steps per captured graph
 
-template <class A, int P, int NB, bool HAS_E>
+// Periodic correction data of a factor for an arithmetic policy (see sweep.cu).
+template <class A>
+struct StepCyc;
+template <>
+struct StepCyc<NativeArith<double>> {
+  static const double* rows(const sb_factor* f) { return f->cyc64; }
+  static double coef(double v) { return v; }
+};
+template <>
+struct StepCyc<DFArith> {
+  static const df* rows(const sb_factor* f) { return reinterpret_cast<const df*>(f->cycdf); }
+  static df coef(double v) {
+    const float h = (float)v;
+    return df{h, (float)(v - (double)h)};
+  }
+};
+
+template <class A, int P, int NB, bool HAS_E, bool CYC>
 int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
                  const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const sb_factor* f = st->fac;
   const int N = (int)f->N;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
-  const size_t smem = ((size_t)2 * (P + 1) * N + (size_t)RW * N) * sizeof(typename A::C);
+  const size_t smem =
+      ((size_t)2 * (P + 1) * N + (size_t)RW * N + (CYC ? (size_t)2 * N : 0)) * sizeof(typename A::C);
   if (smem > 227 * 1024)
     return fail(SB_ERR_UNSUPPORTED, "N=%d too large for the fused step's shared memory", N);
-  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows>;
+  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC>;
   const int threads = 256;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, int> occ;
@@ -249,16 +291,19 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
   if (nb < 1) return fail(SB_ERR_UNSUPPORTED, "fused step kernel cannot be resident");
   const int64_t ntiles = (M + 31) / 32;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
-  k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles);
+  const typename A::C* cy = CYC ? StepCyc<A>::rows(f) : nullptr;  // primal rows (op 0)
+  k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles, cy,
+                                              StepCyc<A>::coef(CYC ? f->cyc_alpha[0] : 0.0),
+                                              StepCyc<A>::coef(CYC ? f->cyc_beta[0] : 0.0));
   return cuda_check(cudaGetLastError(), "fused step launch");
 }
 
-template <class A, int NB, bool HAS_E>
+template <class A, int NB, bool HAS_E, bool CYC>
 int launch_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, double* out,
                int64_t M, int64_t ld, cudaStream_t stream) {
   const int N = (int)st->N;
   dim3 grid((unsigned)((M + 255) / 256), (unsigned)N);
-  rhs_kernel<A, NB, HAS_E><<<grid, 256, 0, stream>>>(rc, N, M, ld, in, out);
+  rhs_kernel<A, NB, HAS_E, CYC><<<grid, 256, 0, stream>>>(rc, N, M, ld, in, out);
   return cuda_check(cudaGetLastError(), "rhs launch");
 }
 
@@ -266,21 +311,26 @@ template <class A>
 int one_step(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
              const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const int P = st->fac->P;
-  if (st->has_e) return launch_fused<A, 2, 0, true>(st, coef, rc, src, state, M, ld, stream);
+  if (st->has_e) return launch_fused<A, 2, 0, true, false>(st, coef, rc, src, state, M, ld, stream);
+  if (P == 1 && st->fac->periodic)
+    return st->NB == 3 ? launch_fused<A, 1, 3, false, true>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false, true>(st, coef, rc, src, state, M, ld, stream);
   if (P == 1)
-    return st->NB == 3 ? launch_fused<A, 1, 3, false>(st, coef, rc, src, state, M, ld, stream)
-                       : launch_fused<A, 1, 0, false>(st, coef, rc, src, state, M, ld, stream);
-  return st->NB == 5 ? launch_fused<A, 2, 5, false>(st, coef, rc, src, state, M, ld, stream)
-                     : launch_fused<A, 2, 0, false>(st, coef, rc, src, state, M, ld, stream);
+    return st->NB == 3 ? launch_fused<A, 1, 3, false, false>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false, false>(st, coef, rc, src, state, M, ld, stream);
+  return st->NB == 5 ? launch_fused<A, 2, 5, false, false>(st, coef, rc, src, state, M, ld, stream)
+                     : launch_fused<A, 2, 0, false, false>(st, coef, rc, src, state, M, ld, stream);
 }
 
 template <class A>
 int one_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, double* out,
             int64_t M, int64_t ld, cudaStream_t stream) {
-  if (st->has_e) return launch_rhs<A, 0, true>(st, rc, in, out, M, ld, stream);
-  if (st->NB == 3) return launch_rhs<A, 3, false>(st, rc, in, out, M, ld, stream);
-  if (st->NB == 5) return launch_rhs<A, 5, false>(st, rc, in, out, M, ld, stream);
-  return launch_rhs<A, 0, false>(st, rc, in, out, M, ld, stream);
+  if (st->has_e) return launch_rhs<A, 0, true, false>(st, rc, in, out, M, ld, stream);
+  if (st->NB == 3)
+    return st->fac->periodic ? launch_rhs<A, 3, false, true>(st, rc, in, out, M, ld, stream)
+                             : launch_rhs<A, 3, false, false>(st, rc, in, out, M, ld, stream);
+  if (st->NB == 5) return launch_rhs<A, 5, false, false>(st, rc, in, out, M, ld, stream);
+  return launch_rhs<A, 0, false, false>(st, rc, in, out, M, ld, stream);
 }
 
 }  // namespace
@@ -316,8 +366,10 @@ int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, doub
   int mat = 0;
   double acoef = coef;
   if (kind == SB_STEP_DIFFUSION) {
-    if (bc != SB_BC_DIRICHLET) return fail(SB_ERR_INVALID_ARG, "diffusion supports SB_BC_DIRICHLET");
-    mat = SB_MAT_DIFFUSION_DIRICHLET;
+    if (bc != SB_BC_DIRICHLET && bc != SB_BC_PERIODIC)
+      return fail(SB_ERR_INVALID_ARG, "diffusion supports SB_BC_DIRICHLET or SB_BC_PERIODIC");
+    if (bc == SB_BC_PERIODIC && N < 3) return fail(SB_ERR_INVALID_ARG, "periodic ends need N >= 3");
+    mat = bc == SB_BC_PERIODIC ? SB_MAT_DIFFUSION_PERIODIC : SB_MAT_DIFFUSION_DIRICHLET;
   } else if (kind == SB_STEP_HYPERDIFFUSION) {
     if (bc != SB_BC_HINGED && bc != SB_BC_TRUNCATED)
       return fail(SB_ERR_INVALID_ARG, "hyperdiffusion supports SB_BC_HINGED or SB_BC_TRUNCATED");
@@ -347,7 +399,10 @@ int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, doub
   st->coef = coef;
   st->dt = dt;
   int rc;
-  if (P == 1)
+  if (P == 1 && mat == SB_MAT_DIFFUSION_PERIODIC)
+    rc = sb_factor_shared_tri_periodic(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N,
+                                       &st->fac);
+  else if (P == 1)
     rc = sb_factor_shared_tri(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N, &st->fac);
   else
     rc = sb_factor_shared_penta(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N,

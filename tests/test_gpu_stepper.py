@@ -19,7 +19,11 @@ def env():
 
 def oracle_run(kind, scheme, bc, N, coef, dt, C, nsteps):
     C = C.copy()
-    if kind == "diffusion":
+    if kind == "diffusion" and bc == "periodic":
+        A = steppers.SharedTriPeriodic(*matrices.diffusion_matrix_periodic(N, coef))
+        for _ in range(nsteps):
+            C = A.solve(C if scheme == "be" else steppers.diffusion_cn_rhs_periodic(N, coef, C))
+    elif kind == "diffusion":
         A = steppers.SharedTri(*matrices.diffusion_matrix(N, coef))
         for _ in range(nsteps):
             C = A.solve(C if scheme == "be" else steppers.diffusion_cn_rhs(N, coef, C))
@@ -37,6 +41,8 @@ def oracle_run(kind, scheme, bc, N, coef, dt, C, nsteps):
 CASES = [
     ("diffusion", "be", "dirichlet", 0.5, 0.0, 1.0),
     ("diffusion", "cn", "dirichlet", 0.4, 0.0, 1.0),
+    ("diffusion", "be", "periodic", 0.5, 0.0, 1.0),
+    ("diffusion", "cn", "periodic", 0.4, 0.0, 1.0),
     ("hyperdiffusion", "be", "hinged", 0.25, 0.0, 1.0),
     ("hyperdiffusion", "cn", "hinged", 0.3, 0.0, 1.0),
     ("hyperdiffusion", "cn", "truncated", 0.3, 0.0, 1.0),
@@ -51,6 +57,8 @@ CASES = [
 @pytest.mark.parametrize("N", [1, 2, 5, 37])
 def test_stepper_matches_oracle(env, kind, scheme, bc, coef, dt, amp, N, arith, mode):
     sb, torch = env
+    if bc == "periodic" and N < 3:
+        pytest.skip("periodic ends need N >= 3")
     M, ld, nsteps = 300, 301, 70  # 70 steps: one 64-step graph plus direct launches
     st = sb.sb_stepper_create(kind, scheme, bc, N, coef, dt)
     C0 = synth.rhs_uniform(seed=N, N=N, M=M, ld=ld, lo=-amp, hi=amp, pad_value=3.5)
@@ -131,3 +139,37 @@ def test_cahn_hilliard_workload_df32(env):
     err, drift = _ch_workload(sb, torch, "df32", synth.WORKLOADS["cahn_hilliard"]["steps"])
     assert np.max(err) <= 1e-10, (np.max(err), np.median(err))
     assert drift <= 1e-10, drift
+
+
+def test_periodic_cn_diffusion_modes_and_mean(env):
+    """Section 3.2's periodic Crank-Nicolson diffusion (the paper's Table 1 scheme):
+    over 100 fused, graphed steps a Fourier mode k is multiplied by
+    ((1 - 4 s sin^2(pi k / N)) / (1 + 4 s sin^2(pi k / N)))^100, and each system's
+    mean is conserved."""
+    sb, torch = env
+    N, s_coef, nsteps = 256, 0.3, 100
+    modes = [0, 1, 5, 64, 127, 128]
+    X = np.concatenate([synth.fourier_mode_block(N, modes, "cos"),
+                        synth.fourier_mode_block(N, modes[1:-1], "sin")], axis=1)
+    ks = np.asarray(modes + modes[1:-1])
+    g = (1.0 - 4.0 * s_coef * np.sin(np.pi * ks / N) ** 2) / (1.0 + 4.0 * s_coef * np.sin(np.pi * ks / N) ** 2)
+    st = sb.sb_stepper_create("diffusion", "cn", "periodic", N, s_coef, 0.0)
+    d = to_dev(X, torch)
+    sb.sb_stepper_run(st, d, nsteps)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_host(d) - X * (g ** nsteps)[None, :])) <= 1e-12
+    C0 = synth.rhs_uniform(seed=3, N=N, M=500)
+    d = to_dev(C0, torch)
+    sb.sb_stepper_run(st, d, nsteps)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_host(d).mean(axis=0) - C0.mean(axis=0))) <= 1e-13
+
+
+def test_periodic_stepper_rejected_by_rollout(env):
+    sb, torch = env
+    st = sb.sb_stepper_create("diffusion", "be", "periodic", 64, 0.5, 0.0)
+    nbytes = sb.sb_rollout_workspace_bytes(st, 8, 4, 2)
+    work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sb.SbError, match="periodic"):
+        sb.sb_rollout_forward(st, torch.zeros((64, 8), dtype=torch.float64, device="cuda"),
+                              torch.zeros((64, 8), dtype=torch.float64, device="cuda"), 4, 2, work)
