@@ -23,6 +23,7 @@ __all__ = [
     "tri_factor", "tri_solve", "tri_solve_adjoint",
     "tri_periodic_factor", "tri_periodic_solve", "tri_periodic_solve_adjoint", "tri_periodic_dense",
     "penta_factor", "penta_solve", "penta_solve_adjoint",
+    "penta_periodic_factor", "penta_periodic_solve", "penta_periodic_solve_adjoint", "penta_periodic_dense",
     "tri_dense", "penta_dense",
 ]
 
@@ -305,3 +306,89 @@ def penta_dense(a, b, c, d, e):
         if i + 2 < N:
             A[i, i + 2] = e[i]
     return A
+
+
+# ----------------------------------------------------------------------------
+# Cyclic pentadiagonal (the periodic matrix of section 5.1's scheme; the paper
+# refers to the literature for its solution)
+# ----------------------------------------------------------------------------
+
+def penta_periodic_dense(a, b, c, d, e):
+    """Dense cyclic pentadiagonal matrix: row i is a_i x_{i-2} + b_i x_{i-1} + c_i x_i
+    + d_i x_{i+1} + e_i x_{i+2} with the indices taken modulo N (N >= 5), so the
+    corner entries are A[0, N-2] = a_0, A[0, N-1] = b_0, A[1, N-1] = a_1,
+    A[N-2, 0] = e_{N-2}, A[N-1, 0] = d_{N-1}, A[N-1, 1] = e_{N-1}."""
+    a, b, c, d, e = (np.asarray(v, dtype=np.float64) for v in (a, b, c, d, e))
+    N = c.shape[0]
+    if N < 5:
+        raise ValueError("a cyclic pentadiagonal matrix needs N >= 5")
+    A = np.zeros((N, N))
+    for i in range(N):
+        for off, v in ((-2, a), (-1, b), (0, c), (1, d), (2, e)):
+            A[i, (i + off) % N] += v[i]
+    return A
+
+
+def penta_periodic_factor(a, b, c, d, e):
+    """Split A = A' + U V^T with a rank-2 correction, the 2 x 2 block form of
+    section 3.3's construction (which is its 1 x 1 case).  With TR the top-right
+    2 x 2 corner block (rows 0,1; columns N-2,N-1), BL the bottom-left one (rows
+    N-2,N-1; columns 0,1) and X = -(the top-left 2 x 2 block of A):
+
+        U = [X; 0; BL]  (rows 0,1 | middle | N-2,N-1),   V = [I; 0; (X^{-1} TR)^T],
+
+    so U V^T puts X X^0 = X in the top-left block, TR and BL in the corners and
+    BL X^{-1} TR in the bottom-right block.  A' = A - U V^T is pentadiagonal (no
+    corners; top-left block 2 A_tl, bottom-right block A_br - BL X^{-1} TR), factored
+    by section 4.1; Z = A'^{-1} U and the 2 x 2 matrix S = I + V^T Z are formed once.
+    Returns a dict with the factors of A' and U, V, Z, S."""
+    a, b, c, d, e = (np.asarray(v, dtype=np.float64).copy() for v in (a, b, c, d, e))
+    N = c.shape[0]
+    if N < 5:
+        raise ValueError("a cyclic pentadiagonal matrix needs N >= 5")
+    A = penta_periodic_dense(a, b, c, d, e)
+    TL = A[0:2, 0:2]
+    TR = A[0:2, N - 2:N]
+    BL = A[N - 2:N, 0:2]
+    X = -TL
+    W = np.linalg.solve(X, TR)  # X^{-1} TR
+    U = np.zeros((N, 2))
+    V = np.zeros((N, 2))
+    U[0:2, :] = X
+    U[N - 2:N, :] = BL
+    V[0:2, :] = np.eye(2)
+    V[N - 2:N, :] = W.T
+    Ap = A - U @ V.T
+    # A' is banded: read its five diagonals back (the corners cancel exactly)
+    ap, bp, cp, dp, ep = (np.zeros(N) for _ in range(5))
+    for i in range(N):
+        if i >= 2:
+            ap[i] = Ap[i, i - 2]
+        if i >= 1:
+            bp[i] = Ap[i, i - 1]
+        cp[i] = Ap[i, i]
+        if i + 1 < N:
+            dp[i] = Ap[i, i + 1]
+        if i + 2 < N:
+            ep[i] = Ap[i, i + 2]
+    fac = penta_factor(ap, bp, cp, dp, ep)
+    Z = penta_solve(*fac, U)
+    S = np.eye(2) + V.T @ Z
+    return {"factors": fac, "U": U, "V": V, "Z": Z, "S": S,
+            "diags_prime": (ap, bp, cp, dp, ep)}
+
+
+def penta_periodic_solve(f, rhs):
+    """Solve A x = rhs (Sherman-Morrison-Woodbury): A' y = rhs,
+    x = y - Z S^{-1} (V^T y)."""
+    y = penta_solve(*f["factors"], rhs)
+    return y - f["Z"] @ np.linalg.solve(f["S"], f["V"].T @ y)
+
+
+def penta_periodic_solve_adjoint(f, g):
+    """Solve A^T y = g (no counterpart in the paper): A^T = A'^T + V U^T, so with
+    w = A'^{-T} g, Z' = A'^{-T} V and S' = I + U^T Z':  y = w - Z' S'^{-1} (U^T w)."""
+    w = penta_solve_adjoint(*f["factors"], g)
+    Zt = penta_solve_adjoint(*f["factors"], f["V"])
+    St = np.eye(2) + f["U"].T @ Zt
+    return w - Zt @ np.linalg.solve(St, f["U"].T @ w)

@@ -32,9 +32,10 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "d2_dirichlet", "d2_noflux", "d2_periodic", "square_tridiag", "d4_truncated",
+    "d2_dirichlet", "d2_noflux", "d2_periodic", "d4_periodic", "square_tridiag", "d4_truncated",
     "diffusion_matrix", "diffusion_matrix_periodic", "hyperdiffusion_matrix", "ch_matrix",
-    "apply_tri", "apply_tri_periodic", "apply_penta", "bands_to_dense",
+    "ch_matrix_periodic", "apply_tri", "apply_tri_periodic", "apply_penta",
+    "apply_penta_periodic", "bands_to_dense",
 ]
 
 
@@ -150,6 +151,29 @@ def ch_matrix(N, sigma):
     return sigma * a, sigma * b, 1.0 + sigma * c, sigma * d, sigma * e
 
 
+def d4_periodic(N):
+    """Periodic fourth difference D2_P @ D2_P: rows (1, -4, 6, -4, 1) everywhere,
+    wrapping around (the operator of section 5.1 with periodic ends).  N >= 5.
+    Formed as the product of two periodic second differences, entry by entry."""
+    if N < 5:
+        raise ValueError("the periodic fourth difference needs N >= 5")
+    D2 = np.zeros((N, N))
+    for i in range(N):
+        D2[i, (i - 1) % N] += 1.0
+        D2[i, i] += -2.0
+        D2[i, (i + 1) % N] += 1.0
+    D4 = D2 @ D2
+    return tuple(np.array([D4[i, (i + off) % N] for i in range(N)]) for off in (-2, -1, 0, 1, 2))
+
+
+def ch_matrix_periodic(N, sigma):
+    """A = I + sigma D4_P: section 5.1's implicit matrix with periodic ends (the
+    paper's own choice, a = e = sigma, b = d = -4 sigma, c = 1 + 6 sigma on every
+    row; the wrapped entries sit in a[0], a[1], b[0], d[N-1], e[N-2], e[N-1])."""
+    a, b, c, d, e = d4_periodic(N)
+    return sigma * a, sigma * b, 1.0 + sigma * c, sigma * d, sigma * e
+
+
 def apply_tri(sub, dia, sup, x):
     """y = T x for a tridiagonal T given by diagonals, x of shape (N, M)."""
     x = np.asarray(x, dtype=np.float64)
@@ -183,6 +207,16 @@ def apply_penta(a, b, c, d, e, x):
     if N > 2:
         y[2:] += a[2:, None] * x[:-2]
         y[:-2] += e[:-2, None] * x[2:]
+    return y
+
+
+def apply_penta_periodic(a, b, c, d, e, x):
+    """y = P x for a cyclic pentadiagonal P (indices modulo N), x of shape (N, M)."""
+    x = np.asarray(x, dtype=np.float64)
+    N = x.shape[0]
+    y = np.zeros_like(x)
+    for off, v in ((-2, a), (-1, b), (0, c), (1, d), (2, e)):
+        y += np.asarray(v)[:, None] * np.roll(x, -off, axis=0)
     return y
 
 
