@@ -105,6 +105,27 @@ int sb_factor_shared_tri_periodic(int64_t N, const double* a, const double* b, c
                                   sb_factor** out);
 
 /*
+ * sb_factor_shared_penta_periodic -- factorise a shared cyclic pentadiagonal matrix:
+ * row i is a[i] x[i-2] + b[i] x[i-1] + c[i] x[i] + d[i] x[i+1] + e[i] x[i+2] with the
+ * indices modulo N (N >= 5), so a[0], a[1], b[0], d[N-1], e[N-2], e[N-1] are corner
+ * entries.  Section 5.1's scheme is periodic and the paper refers to the literature
+ * for this solve; this library uses the 2 x 2 block form of section 3.3's split:
+ * A = A' + U V^T with X = -(top-left 2 x 2 block), U = [X; 0; BL], V = [I; 0;
+ * (X^{-1} TR)^T] (TR, BL the corner blocks), A' pentadiagonal (top-left block doubled,
+ * bottom-right block minus BL X^{-1} TR, no corners) factored as by
+ * sb_factor_shared_penta, and Z = A'^{-1} U and S = I + V^T Z formed once in FP64.
+ * Every solve returns x = y - Z S^{-1} V^T y with y = A'^{-1} b in one pass: y_0 and
+ * y_1 are accumulated as dot products during the forward sweep, and the first two
+ * rows of the backward sweep are held back until the correction is known.  The
+ * transpose uses A^T = A'^T + V U^T (no counterpart in the paper).  Refinement and
+ * group solves reject periodic handles; the partitioned algorithm falls back to the
+ * sweeps.  SB_ERR_SINGULAR for a singular top-left block, a zero pivot of A' or a
+ * singular S.
+ */
+int sb_factor_shared_penta_periodic(int64_t N, const double* a, const double* b, const double* c,
+                                    const double* d, const double* e, sb_factor** out);
+
+/*
  * sb_factor_shared_penta -- factorise a shared pentadiagonal matrix A = L R
  * (section 4.1; Algorithm 3 read with the section's equations).
  *
@@ -247,6 +268,10 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
  *   SB_MAT_DIFFUSION_PERIODIC   K = tridiag(-1, 2, -1) wrapping around (section 3.3's
  *                               matrix; N >= 3): a[0] and c[N-1] are the corner
  *                               entries; factor it with sb_factor_shared_tri_periodic.
+ *   SB_MAT_CH_PERIODIC          K = D2P * D2P, rows (1, -4, 6, -4, 1) wrapping around:
+ *                               section 5.1's implicit matrix with the paper's periodic
+ *                               ends (N >= 5); factor it with
+ *                               sb_factor_shared_penta_periodic.
  * `diags` is a host array of (2P+1)*N doubles (P = 1 for the diffusion matrices, 2
  * otherwise), diagonal-major: diags[k*N + i] is row i of the diagonal at offset
  * k - P; entries outside the matrix are written as 0 (except the periodic
@@ -258,6 +283,7 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
 #define SB_MAT_HYPER_TRUNCATED     3
 #define SB_MAT_CH_NOFLUX           4
 #define SB_MAT_DIFFUSION_PERIODIC  5
+#define SB_MAT_CH_PERIODIC         6
 int sb_build_matrix(int kind, int64_t N, double coef, double* diags);
 
 /*
@@ -353,12 +379,15 @@ int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const*
  *                          K wraps around, A is factored as by
  *                          sb_factor_shared_tri_periodic and every step applies the
  *                          Sherman-Morrison correction inside the fused kernel).
- *   SB_STEP_HYPERDIFFUSION A = I + coef D4 with bc SB_BC_HINGED (D4 = D2 D2) or
- *                          SB_BC_TRUNCATED (Toeplitz 1,-4,6,-4,1); B = I (BE) or
- *                          I - coef D4 (section 4.2's Crank-Nicolson).
- *   SB_STEP_CAHN_HILLIARD  section 5.1's semi-implicit scheme with no-flux ends
- *                          (bc SB_BC_NOFLUX, scheme SB_SCHEME_BE): A = I + dt coef D4_N,
- *                          B = I, E = dt D2_N, with coef = gamma in grid units (dx = 1).
+ *   SB_STEP_HYPERDIFFUSION A = I + coef D4 with bc SB_BC_HINGED (D4 = D2 D2),
+ *                          SB_BC_TRUNCATED (Toeplitz 1,-4,6,-4,1) or SB_BC_PERIODIC
+ *                          (D4 = D2P D2P wrapping around, N >= 5, the cyclic
+ *                          pentadiagonal solve of sb_factor_shared_penta_periodic);
+ *                          B = I (BE) or I - coef D4 (section 4.2's Crank-Nicolson).
+ *   SB_STEP_CAHN_HILLIARD  section 5.1's semi-implicit scheme (scheme SB_SCHEME_BE):
+ *                          A = I + dt coef D4, B = I, E = dt D2, with coef = gamma in
+ *                          grid units (dx = 1); bc SB_BC_NOFLUX (D2 = D2_N, D4 = D2_N^2)
+ *                          or SB_BC_PERIODIC (the paper's own ends: D2_P, D4_P, N >= 5).
  * The stepper owns the factorised A and the right-hand-side coefficients.
  */
 typedef struct sb_stepper sb_stepper;

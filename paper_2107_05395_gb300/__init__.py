@@ -16,7 +16,7 @@ from ._lib import (  # noqa: F401
     SB_ERR_ALLOC, SB_ERR_CUDA, SB_ERR_INVALID_ARG, SB_ERR_SINGULAR, SB_ERR_UNSUPPORTED,
     SB_F32, SB_F64, SB_OK, SIGNATURES, MATRIX_KINDS, Factor, SbError, lib, sb_build_matrix,
     sb_factor_info,
-    sb_factor_shared_penta, sb_factor_shared_tri, sb_factor_shared_tri_periodic, sb_last_error, sb_solve_batched,
+    sb_factor_shared_penta, sb_factor_shared_tri, sb_factor_shared_tri_periodic, sb_factor_shared_penta_periodic, sb_last_error, sb_solve_batched,
     sb_solve_batched_adjoint, sb_solve_batched_ex, sb_version, SB_ARITH_NATIVE, SB_ARITH_DF32,
     Shape, SB_ALGO_SEQUENTIAL, SB_ALGO_PARTITIONED, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run,
     sb_refine_workspace_bytes, sb_solve_batched_refined, sb_solve_batched_groups,

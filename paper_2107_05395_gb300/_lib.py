@@ -32,7 +32,9 @@ SB_MAT_HYPER_HINGED = 2
 SB_MAT_HYPER_TRUNCATED = 3
 SB_MAT_CH_NOFLUX = 4
 SB_MAT_DIFFUSION_PERIODIC = 5
-MATRIX_KINDS = {"diffusion": 1, "hinged": 2, "truncated": 3, "ch_noflux": 4, "diffusion_periodic": 5}
+SB_MAT_CH_PERIODIC = 6
+MATRIX_KINDS = {"diffusion": 1, "hinged": 2, "truncated": 3, "ch_noflux": 4, "diffusion_periodic": 5,
+                "ch_periodic": 6}
 
 _ERR_NAMES = {
     SB_ERR_INVALID_ARG: "SB_ERR_INVALID_ARG",
@@ -62,6 +64,8 @@ SIGNATURES = {
     "sb_factor_shared_tri": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
     "sb_factor_shared_tri_periodic": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
     "sb_factor_shared_penta": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_vp)]),
+    "sb_factor_shared_penta_periodic": (ctypes.c_int, [_c_i64, _dp, _dp, _dp, _dp, _dp,
+                                                       ctypes.POINTER(_vp)]),
     "sb_factor_destroy": (None, [_vp]),
     "sb_factor_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_c_i64)]),
     "sb_solve_batched": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, ctypes.c_int, _vp]),
@@ -216,6 +220,18 @@ def sb_factor_shared_tri_periodic(a, b, c) -> Factor:
     _check(lib().sb_factor_shared_tri_periodic(N, *[x.ctypes.data_as(_dp) for x in arrs],
                                                ctypes.byref(h)))
     return Factor(h.value, 1, N, arrs)
+
+
+def sb_factor_shared_penta_periodic(a, b, c, d, e) -> Factor:
+    """Factorise a shared cyclic pentadiagonal matrix (indices modulo N; a[0], a[1],
+    b[0], d[N-1], e[N-2], e[N-1] are the corner entries).  Solves with the handle
+    apply the rank-2 Sherman-Morrison-Woodbury correction."""
+    N = len(c)
+    arrs = [_host_f64(v, N) for v in (a, b, c, d, e)]
+    h = ctypes.c_void_p()
+    _check(lib().sb_factor_shared_penta_periodic(N, *[x.ctypes.data_as(_dp) for x in arrs],
+                                                 ctypes.byref(h)))
+    return Factor(h.value, 2, N, arrs)
 
 
 def sb_factor_shared_penta(a, b, c, d, e) -> Factor:

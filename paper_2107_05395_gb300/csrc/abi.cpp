@@ -412,6 +412,15 @@ int build_matrix(int kind, int64_t N, double coef, std::vector<double>& diags, i
       diags.assign(3 * N, -coef);  // the corners a[0], c[N-1] included
       for (int64_t i = 0; i < N; ++i) diags[N + i] = 1.0 + 2.0 * coef;
       return SB_OK;
+    case SB_MAT_CH_PERIODIC: {
+      if (N < 5) return fail(SB_ERR_INVALID_ARG, "the periodic matrix needs N >= 5");
+      *P = 2;
+      const double st[5] = {1.0, -4.0, 6.0, -4.0, 1.0};  // D2_P D2_P, wrapping around
+      diags.assign(5 * N, 0.0);
+      for (int k = 0; k < 5; ++k)
+        for (int64_t i = 0; i < N; ++i) diags[k * N + i] = (k == 2 ? 1.0 : 0.0) + coef * st[k];
+      return SB_OK;
+    }
     case SB_MAT_HYPER_HINGED:
       square_tridiagonal(N, lo, mid, up, K);
       break;
@@ -539,6 +548,7 @@ int sb_factor_shared_tri_periodic(int64_t N, const double* a, const double* b, c
   const double* d[3] = {ap.data(), bp.data(), cp.data()};
   sb_factor* f = nullptr;
   SB_TRY(make_factor(1, N, d, &f, true));
+  f->periodic_rank = 1;
   // correction data, per op: rows (w_i, -z_i), alpha, beta (see sb_factor)
   std::vector<double> e0(N, 0.0), z, w, zt, wt;
   e0[0] = 1.0;
@@ -588,6 +598,167 @@ int sb_factor_shared_tri_periodic(int64_t N, const double* a, const double* b, c
       rc = cuda_check(cudaMemcpy(f->cyc32, h32.data(), 4 * N * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
     if (rc == SB_OK)
       rc = cuda_check(cudaMemcpy(f->cycdf, hdf.data(), 8 * N * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  }
+  if (rc != SB_OK) {
+    sb_factor_destroy(f);
+    return rc;
+  }
+  *out = f;
+  return SB_OK;
+}
+
+// Solve of a pentadiagonal matrix given diagonal-major (5 N values, offsets -2..2),
+// by the section 4.1 recurrence (host, FP64, for the periodic correction vectors).
+static bool penta_solve_host(int64_t N, const std::vector<double>& dg, std::vector<double> r,
+                             std::vector<double>& x) {
+  auto D = [&](int k, int64_t i) { return dg[(size_t)k * N + i]; };
+  std::vector<double> al(N), be(N), ga(N, 0.0), de(N, 0.0), ep(N);
+  for (int64_t i = 0; i < N; ++i) {
+    const double ai = i >= 2 ? D(0, i) : 0.0, bi = i >= 1 ? D(1, i) : 0.0;
+    const double di = i + 1 < N ? D(3, i) : 0.0, ei = i + 2 < N ? D(4, i) : 0.0;
+    be[i] = bi - ai * (i >= 2 ? ga[i - 2] : 0.0);
+    al[i] = D(2, i) - ai * (i >= 2 ? de[i - 2] : 0.0) - be[i] * (i >= 1 ? ga[i - 1] : 0.0);
+    if (al[i] == 0.0 || !std::isfinite(al[i])) return false;
+    ga[i] = (di - be[i] * (i >= 1 ? de[i - 1] : 0.0)) / al[i];
+    de[i] = ei / al[i];
+    ep[i] = ai;
+  }
+  for (int64_t i = 0; i < N; ++i)
+    r[i] = (r[i] - (i >= 1 ? be[i] * r[i - 1] : 0.0) - (i >= 2 ? ep[i] * r[i - 2] : 0.0)) / al[i];
+  x.assign(N, 0.0);
+  for (int64_t i = N - 1; i >= 0; --i)
+    x[i] = r[i] - (i + 1 < N ? ga[i] * x[i + 1] : 0.0) - (i + 2 < N ? de[i] * x[i + 2] : 0.0);
+  return true;
+}
+
+int sb_factor_shared_penta_periodic(int64_t N, const double* a, const double* b, const double* c,
+                                    const double* d, const double* e, sb_factor** out) {
+  clear_error();
+  if (out == nullptr) return fail(SB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 5)
+    return fail(SB_ERR_INVALID_ARG, "a cyclic pentadiagonal matrix needs N >= 5 (got %lld)", (long long)N);
+  const double* in[5] = {a, b, c, d, e};
+  for (int k = 0; k < 5; ++k) {
+    if (!in[k]) return fail(SB_ERR_INVALID_ARG, "diagonal %d is NULL", k);
+    if (!finite_all(in[k], 0, N)) return fail(SB_ERR_INVALID_ARG, "diagonal %d has a non-finite entry", k);
+  }
+  // corner blocks (row-major 2 x 2): TL rows/cols 0,1; TR rows 0,1 x cols N-2,N-1;
+  // BL rows N-2,N-1 x cols 0,1
+  const double TL[4] = {c[0], d[0], b[1], c[1]};
+  const double TR[4] = {a[0], b[0], 0.0, a[1]};
+  const double BL[4] = {e[N - 2], 0.0, d[N - 1], e[N - 1]};
+  // X = -TL, W = X^{-1} TR; U = [X; 0; BL], V = [I; 0; W^T] (rank 2)
+  const double X[4] = {-TL[0], -TL[1], -TL[2], -TL[3]};
+  const double detX = X[0] * X[3] - X[1] * X[2];
+  if (detX == 0.0 || !std::isfinite(detX))
+    return fail(SB_ERR_SINGULAR, "the top-left 2 x 2 block is singular: the rank-2 split needs it invertible");
+  const double Xi[4] = {X[3] / detX, -X[1] / detX, -X[2] / detX, X[0] / detX};
+  double W[4], BW[4];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) W[2 * i + j] = Xi[2 * i] * TR[j] + Xi[2 * i + 1] * TR[2 + j];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) BW[2 * i + j] = BL[2 * i] * W[j] + BL[2 * i + 1] * W[2 + j];
+  // A' = A - U V^T: corners removed, top-left block 2 TL, bottom-right block BR - BL W
+  std::vector<double> dg((size_t)5 * N);
+  for (int k = 0; k < 5; ++k)
+    for (int64_t i = 0; i < N; ++i) {
+      const int64_t j = i + (k - 2);
+      dg[(size_t)k * N + i] = (j >= 0 && j < N) ? in[k][i] : 0.0;
+    }
+  auto at = [&](int off, int64_t i) -> double& { return dg[(size_t)(off + 2) * N + i]; };
+  at(0, 0) = 2.0 * c[0];
+  at(1, 0) = 2.0 * d[0];
+  at(-1, 1) = 2.0 * b[1];
+  at(0, 1) = 2.0 * c[1];
+  at(0, N - 2) -= BW[0];
+  at(1, N - 2) -= BW[1];
+  at(-1, N - 1) -= BW[2];
+  at(0, N - 1) -= BW[3];
+  const double* dp[5] = {&dg[0], &dg[N], &dg[2 * N], &dg[3 * N], &dg[4 * N]};
+  sb_factor* f = nullptr;
+  SB_TRY(make_factor(2, N, dp, &f, true));
+  f->periodic_rank = 2;
+  // U and V as N x 2 (column-major vectors)
+  std::vector<double> U0(N, 0.0), U1(N, 0.0), V0(N, 0.0), V1(N, 0.0), e0(N, 0.0), e1(N, 0.0);
+  U0[0] = X[0]; U1[0] = X[1]; U0[1] = X[2]; U1[1] = X[3];
+  U0[N - 2] = BL[0]; U1[N - 2] = BL[1]; U0[N - 1] = BL[2]; U1[N - 1] = BL[3];
+  V0[0] = 1.0; V1[1] = 1.0;
+  // V[N-2:N, :] = W^T: V_k[N-2+r] = W[k][r]
+  V0[N - 2] = W[0]; V1[N - 2] = W[2]; V0[N - 1] = W[1]; V1[N - 1] = W[3];
+  e0[0] = 1.0;
+  e1[1] = 1.0;
+  const std::vector<double> dgT = transpose_diagonals(2, (int)N, dg.data());
+  std::vector<double> z0, z1, w0, w1, zt0, zt1, wt0, wt1;
+  const bool ok = penta_solve_host(N, dg, U0, z0) && penta_solve_host(N, dg, U1, z1) &&
+                  penta_solve_host(N, dgT, e0, w0) && penta_solve_host(N, dgT, e1, w1) &&
+                  penta_solve_host(N, dgT, V0, zt0) && penta_solve_host(N, dgT, V1, zt1) &&
+                  penta_solve_host(N, dg, e0, wt0) && penta_solve_host(N, dg, e1, wt1);
+  // per op: rows (w0, w1, -z0, -z1) and 12 scalars P (2x2), Q (2x2), S^{-1} (2x2) with
+  // g = S^{-1} (P (y_0, y_1) + Q (y_{N-2}, y_{N-1})), x = y - z0 g_0 - z1 g_1
+  auto dot = [&](const std::vector<double>& p, const std::vector<double>& q) {
+    double t = 0.0;
+    for (int64_t i = 0; i < N; ++i) t += p[i] * q[i];
+    return t;
+  };
+  double S[4], St[4];
+  if (ok) {
+    S[0] = 1.0 + dot(V0, z0); S[1] = dot(V0, z1); S[2] = dot(V1, z0); S[3] = 1.0 + dot(V1, z1);
+    St[0] = 1.0 + dot(U0, zt0); St[1] = dot(U0, zt1); St[2] = dot(U1, zt0); St[3] = 1.0 + dot(U1, zt1);
+  }
+  const double dS = ok ? S[0] * S[3] - S[1] * S[2] : 0.0, dSt = ok ? St[0] * St[3] - St[1] * St[2] : 0.0;
+  if (!ok || dS == 0.0 || dSt == 0.0 || !std::isfinite(dS) || !std::isfinite(dSt)) {
+    sb_factor_destroy(f);
+    return fail(SB_ERR_SINGULAR, "the cyclic matrix is singular (I + V^T A'^{-1} U)");
+  }
+  const size_t per_op = 4 * (size_t)N + 12;
+  std::vector<double> h(2 * per_op, 0.0);
+  auto fill = [&](double* o, const std::vector<double>& wa, const std::vector<double>& wb,
+                  const std::vector<double>& za, const std::vector<double>& zb, const double* P,
+                  const double* Q, const double* Sm, double det) {
+    for (int64_t i = 0; i < N; ++i) {
+      o[4 * i] = wa[i];
+      o[4 * i + 1] = wb[i];
+      o[4 * i + 2] = -za[i];
+      o[4 * i + 3] = -zb[i];
+    }
+    double* sc = o + 4 * N;
+    for (int k = 0; k < 4; ++k) {
+      sc[k] = P[k];
+      sc[4 + k] = Q[k];
+    }
+    sc[8] = Sm[3] / det;
+    sc[9] = -Sm[1] / det;
+    sc[10] = -Sm[2] / det;
+    sc[11] = Sm[0] / det;
+  };
+  // primal: V^T y = (y_0, y_1) + W (y_{N-2}, y_{N-1})
+  const double Ip[4] = {1.0, 0.0, 0.0, 1.0};
+  fill(h.data(), w0, w1, z0, z1, Ip, W, S, dS);
+  // adjoint: U^T y = X^T (y_0, y_1) + BL^T (y_{N-2}, y_{N-1})
+  const double XT[4] = {X[0], X[2], X[1], X[3]}, BLT[4] = {BL[0], BL[2], BL[1], BL[3]};
+  fill(h.data() + per_op, wt0, wt1, zt0, zt1, XT, BLT, St, dSt);
+  std::vector<float> h32(h.size()), hdf(2 * h.size());
+  for (size_t k = 0; k < h.size(); ++k) {
+    h32[k] = (float)h[k];
+    hdf[2 * k] = (float)h[k];
+    hdf[2 * k + 1] = (float)(h[k] - (double)hdf[2 * k]);
+  }
+  int rc = SB_OK;
+  {
+    DeviceGuard g(f->device);
+    rc = g.rc;
+    void* mem = nullptr;
+    const size_t n = h.size();
+    if (rc == SB_OK) rc = cuda_check(cudaMalloc(&mem, n * 8 + n * 4 + 2 * n * 4), "cudaMalloc");
+    if (rc == SB_OK) {
+      f->cyc64 = static_cast<double*>(mem);
+      f->cyc32 = reinterpret_cast<float*>(f->cyc64 + n);
+      f->cycdf = f->cyc32 + n;
+      rc = cuda_check(cudaMemcpy(f->cyc64, h.data(), n * 8, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+    if (rc == SB_OK) rc = cuda_check(cudaMemcpy(f->cyc32, h32.data(), n * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (rc == SB_OK) rc = cuda_check(cudaMemcpy(f->cycdf, hdf.data(), 2 * n * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
   }
   if (rc != SB_OK) {
     sb_factor_destroy(f);

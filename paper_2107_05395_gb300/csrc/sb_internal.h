@@ -94,8 +94,12 @@ struct sb_factor {
   // solve applies the Sherman-Morrison correction x = y - f z with
   // f = beta (y_0 + alpha y_{N-1}) and y_0 = w . rhs accumulated in the forward
   // sweep.  Per op (A, A^T): rows (w_i, -z_i) on the device, alpha and beta on the host.
+  // Cyclic pentadiagonal (rank 2): per op, rows (w0_i, w1_i, -z0_i, -z1_i) and then
+  // 12 scalars P, Q, S^{-1} (2 x 2 each): g = S^{-1} (P (y_0, y_1) + Q (y_{N-2}, y_{N-1})),
+  // x = y - z0 g_0 - z1 g_1.
   bool periodic = false;
-  double* cyc64 = nullptr;  // device: [op][N][2], FP64
+  int periodic_rank = 0;    // 1 (tridiagonal) or 2 (pentadiagonal)
+  double* cyc64 = nullptr;  // device: per op, N rows (2 or 4 values) [+ 12 scalars], FP64
   float* cyc32 = nullptr;   // device: the same rounded to FP32
   float* cycdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   double cyc_alpha[2] = {0.0, 0.0}, cyc_beta[2] = {0.0, 0.0};

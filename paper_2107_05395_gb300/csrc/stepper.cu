@@ -40,10 +40,16 @@ struct StConv<DFArith, double> {
 
 // rcoef rows: if NB > 0, NB values per row (B at offsets -(NB/2)..NB/2), then if
 // HAS_E, 3 values per row (E at offsets -1..1).  Out-of-matrix entries are 0.
-// CYC: periodic ends (section 3.3): the window wraps (row -1 is row N-1, row N is
-// row 0) and the solve applies the Sherman-Morrison correction with the factor's
-// rows cyc = (w_i, -z_i) and scalars alpha, beta (see sweep_tile.cuh).
-template <class A, int P, int NB, bool HAS_E, int R, bool CYC>
+// CYC: periodic ends: the window wraps (rows -2, -1 are rows N-2, N-1; rows N, N+1
+// are rows 0, 1) and the solve applies the factor's correction: rank 1 (the
+// tridiagonal matrix of section 3.3, rows cyc = (w_i, -z_i), scalars alpha, beta)
+// or rank 2 (cyclic pentadiagonal, rows (w0_i, w1_i, -z0_i, -z1_i) and 12 scalars
+// after them); see sweep_tile.cuh.
+__host__ __device__ constexpr int step_cyc_len(int rank, int N) {
+  return rank == 1 ? 2 * N : rank == 2 ? 4 * N + 12 : 0;
+}
+
+template <class A, int P, int NB, bool HAS_E, int R, int CYC>
 __global__ void __launch_bounds__(512)
 fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
                   int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles,
@@ -61,8 +67,8 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     const int n = 2 * W * N;
     for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
     for (int k = threadIdx.x; k < RW * N; k += blockDim.x) cs[n + k] = rcoef[k];
-    if constexpr (CYC)
-      for (int k = threadIdx.x; k < 2 * N; k += blockDim.x) cs[n + RW * N + k] = cyc[k];
+    if constexpr (CYC != 0)
+      for (int k = threadIdx.x; k < step_cyc_len(CYC, N); k += blockDim.x) cs[n + RW * N + k] = cyc[k];
   }
   __syncthreads();
   const C* fw = cs;
@@ -102,7 +108,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         pw[2] = A::cubic(cw[3]);  // phi(C_{i+1}) once C_{i+1} entered the window
       }
     };
-    V u1 = A::zero(), u2 = A::zero(), dot = A::zero();
+    V u1 = A::zero(), u2 = A::zero(), dot = A::zero(), dot1 = A::zero();
     auto build_and_sweep = [&](int i) {
       V r;
       if constexpr (NB > 0) {
@@ -120,7 +126,11 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         r = A::fmac(e[2], pw[2], r);
       }
       const V u = A::template step<P, false>(fw + W * i, r, u1, u2);
-      if constexpr (CYC) dot = A::fmac(cy[2 * i], r, dot);
+      if constexpr (CYC == 1) dot = A::fmac(cy[2 * i], r, dot);
+      if constexpr (CYC == 2) {
+        dot = A::fmac(cy[4 * i], r, dot);
+        dot1 = A::fmac(cy[4 * i + 1], r, dot1);
+      }
       *reinterpret_cast<S*>(y + (int64_t)i * ld) = A::to_store(u);
       u2 = u1;
       u1 = u;
@@ -130,11 +140,13 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     // forward sweep overwrites anything)
     load_rows(va, 0);
     load_rows(vb, R);
-    double c0 = 0.0;
-    if constexpr (CYC) {
+    double c0 = 0.0, c1 = 0.0;
+    if constexpr (CYC != 0) {
       c0 = va[0];
+      c1 = va[1];  // N >= 3 (rank 1) or 5 (rank 2), and R >= 2
       // three pushes (rows 0, 1, 2) precede the build of row 0 and each shifts the
-      // window left by one, so the last slot now ends up holding row -1
+      // window left by one, so the last two slots end up holding rows -2 and -1
+      cw[3] = StConv<A, double>::in(c[(int64_t)(N - 2) * ld]);
       cw[4] = StConv<A, double>::in(c[(int64_t)(N - 1) * ld]);
     }
     push(N > 0 ? va[0] : 0.0);
@@ -146,7 +158,8 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 + j;
         if (i < N) {
           const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R]) : (CYC && i + 2 == N ? c0 : 0.0);
+          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R])
+                                       : (CYC != 0 ? (i + 2 == N ? c0 : c1) : 0.0);
           push(v);
           build_and_sweep(i);
         }
@@ -157,7 +170,8 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 + R + j;
         if (i < N) {
           const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R]) : (CYC && i + 2 == N ? c0 : 0.0);
+          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R])
+                                       : (CYC != 0 ? (i + 2 == N ? c0 : c1) : 0.0);
           push(v);
           build_and_sweep(i);
         }
@@ -166,7 +180,7 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     }
 
     // backward sweep (B0 == 1 for the primal factors)
-    V x1 = A::zero(), x2 = A::zero(), fc = A::zero();
+    V x1 = A::zero(), x2 = A::zero(), fc = A::zero(), g1 = A::zero();
     S sa[R], sb_[R];
     auto load_mid = [&](S (&buf)[R], int i0) {
 #pragma unroll
@@ -179,9 +193,22 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
         const int i = i0 - j;
         if (i >= 0) {
           const V xi = A::template step<P, true>(bw + W * i, A::from_store(buf[j]), x1, x2);
-          if constexpr (CYC) {
+          if constexpr (CYC == 1) {
             if (i == N - 1) fc = A::mulc(beta, A::fmac(alpha, xi, dot));
             y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[2 * i + 1], fc, xi));
+          } else if constexpr (CYC == 2) {
+            if (i < N - 2) {
+              y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
+            } else if (i == N - 2) {  // x1 holds y_{N-1}
+              const C* sc = cy + 4 * N;
+              const V t0 = A::fmac(sc[0], dot, A::fmac(sc[1], dot1, A::fmac(sc[4], xi, A::mulc(sc[5], x1))));
+              const V t1 = A::fmac(sc[2], dot, A::fmac(sc[3], dot1, A::fmac(sc[6], xi, A::mulc(sc[7], x1))));
+              fc = A::fmac(sc[8], t0, A::mulc(sc[9], t1));
+              g1 = A::fmac(sc[10], t0, A::mulc(sc[11], t1));
+              const int j1 = N - 1;
+              y[(int64_t)j1 * ld] = StConv<A, double>::out(A::fmac(cy[4 * j1 + 3], g1, A::fmac(cy[4 * j1 + 2], fc, x1)));
+              y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
+            }
           } else {
             y[(int64_t)i * ld] = StConv<A, double>::out(xi);
           }
@@ -261,14 +288,14 @@ struct StepCyc<DFArith> {
   }
 };
 
-template <class A, int P, int NB, bool HAS_E, bool CYC>
+template <class A, int P, int NB, bool HAS_E, int CYC>
 int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
                  const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const sb_factor* f = st->fac;
   const int N = (int)f->N;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
   const size_t smem =
-      ((size_t)2 * (P + 1) * N + (size_t)RW * N + (CYC ? (size_t)2 * N : 0)) * sizeof(typename A::C);
+      ((size_t)2 * (P + 1) * N + (size_t)RW * N + (size_t)step_cyc_len(CYC, N)) * sizeof(typename A::C);
   if (smem > 227 * 1024)
     return fail(SB_ERR_UNSUPPORTED, "N=%d too large for the fused step's shared memory", N);
   auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC>;
@@ -311,25 +338,36 @@ template <class A>
 int one_step(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
              const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
   const int P = st->fac->P;
-  if (st->has_e) return launch_fused<A, 2, 0, true, false>(st, coef, rc, src, state, M, ld, stream);
-  if (P == 1 && st->fac->periodic)
-    return st->NB == 3 ? launch_fused<A, 1, 3, false, true>(st, coef, rc, src, state, M, ld, stream)
-                       : launch_fused<A, 1, 0, false, true>(st, coef, rc, src, state, M, ld, stream);
+  const bool per = st->fac->periodic;
+  if (st->has_e)
+    return per ? launch_fused<A, 2, 0, true, 2>(st, coef, rc, src, state, M, ld, stream)
+               : launch_fused<A, 2, 0, true, 0>(st, coef, rc, src, state, M, ld, stream);
+  if (P == 1 && per)
+    return st->NB == 3 ? launch_fused<A, 1, 3, false, 1>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false, 1>(st, coef, rc, src, state, M, ld, stream);
   if (P == 1)
-    return st->NB == 3 ? launch_fused<A, 1, 3, false, false>(st, coef, rc, src, state, M, ld, stream)
-                       : launch_fused<A, 1, 0, false, false>(st, coef, rc, src, state, M, ld, stream);
-  return st->NB == 5 ? launch_fused<A, 2, 5, false, false>(st, coef, rc, src, state, M, ld, stream)
-                     : launch_fused<A, 2, 0, false, false>(st, coef, rc, src, state, M, ld, stream);
+    return st->NB == 3 ? launch_fused<A, 1, 3, false, 0>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 1, 0, false, 0>(st, coef, rc, src, state, M, ld, stream);
+  if (per)
+    return st->NB == 5 ? launch_fused<A, 2, 5, false, 2>(st, coef, rc, src, state, M, ld, stream)
+                       : launch_fused<A, 2, 0, false, 2>(st, coef, rc, src, state, M, ld, stream);
+  return st->NB == 5 ? launch_fused<A, 2, 5, false, 0>(st, coef, rc, src, state, M, ld, stream)
+                     : launch_fused<A, 2, 0, false, 0>(st, coef, rc, src, state, M, ld, stream);
 }
 
 template <class A>
 int one_rhs(const sb_stepper* st, const typename A::C* rc, const double* in, double* out,
             int64_t M, int64_t ld, cudaStream_t stream) {
-  if (st->has_e) return launch_rhs<A, 0, true, false>(st, rc, in, out, M, ld, stream);
+  const bool per = st->fac->periodic;
+  if (st->has_e)
+    return per ? launch_rhs<A, 0, true, true>(st, rc, in, out, M, ld, stream)
+               : launch_rhs<A, 0, true, false>(st, rc, in, out, M, ld, stream);
   if (st->NB == 3)
-    return st->fac->periodic ? launch_rhs<A, 3, false, true>(st, rc, in, out, M, ld, stream)
-                             : launch_rhs<A, 3, false, false>(st, rc, in, out, M, ld, stream);
-  if (st->NB == 5) return launch_rhs<A, 5, false, false>(st, rc, in, out, M, ld, stream);
+    return per ? launch_rhs<A, 3, false, true>(st, rc, in, out, M, ld, stream)
+               : launch_rhs<A, 3, false, false>(st, rc, in, out, M, ld, stream);
+  if (st->NB == 5)
+    return per ? launch_rhs<A, 5, false, true>(st, rc, in, out, M, ld, stream)
+               : launch_rhs<A, 5, false, false>(st, rc, in, out, M, ld, stream);
   return launch_rhs<A, 0, false, false>(st, rc, in, out, M, ld, stream);
 }
 
@@ -371,15 +409,20 @@ int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, doub
     if (bc == SB_BC_PERIODIC && N < 3) return fail(SB_ERR_INVALID_ARG, "periodic ends need N >= 3");
     mat = bc == SB_BC_PERIODIC ? SB_MAT_DIFFUSION_PERIODIC : SB_MAT_DIFFUSION_DIRICHLET;
   } else if (kind == SB_STEP_HYPERDIFFUSION) {
-    if (bc != SB_BC_HINGED && bc != SB_BC_TRUNCATED)
-      return fail(SB_ERR_INVALID_ARG, "hyperdiffusion supports SB_BC_HINGED or SB_BC_TRUNCATED");
-    mat = bc == SB_BC_HINGED ? SB_MAT_HYPER_HINGED : SB_MAT_HYPER_TRUNCATED;
+    if (bc != SB_BC_HINGED && bc != SB_BC_TRUNCATED && bc != SB_BC_PERIODIC)
+      return fail(SB_ERR_INVALID_ARG,
+                  "hyperdiffusion supports SB_BC_HINGED, SB_BC_TRUNCATED or SB_BC_PERIODIC");
+    if (bc == SB_BC_PERIODIC && N < 5) return fail(SB_ERR_INVALID_ARG, "periodic ends need N >= 5");
+    mat = bc == SB_BC_HINGED ? SB_MAT_HYPER_HINGED
+                             : (bc == SB_BC_TRUNCATED ? SB_MAT_HYPER_TRUNCATED : SB_MAT_CH_PERIODIC);
   } else if (kind == SB_STEP_CAHN_HILLIARD) {
-    if (bc != SB_BC_NOFLUX) return fail(SB_ERR_INVALID_ARG, "Cahn-Hilliard supports SB_BC_NOFLUX");
+    if (bc != SB_BC_NOFLUX && bc != SB_BC_PERIODIC)
+      return fail(SB_ERR_INVALID_ARG, "Cahn-Hilliard supports SB_BC_NOFLUX or SB_BC_PERIODIC");
+    if (bc == SB_BC_PERIODIC && N < 5) return fail(SB_ERR_INVALID_ARG, "periodic ends need N >= 5");
     if (scheme != SB_SCHEME_BE)
       return fail(SB_ERR_INVALID_ARG, "Cahn-Hilliard uses the semi-implicit scheme (SB_SCHEME_BE)");
     if (!(dt > 0.0)) return fail(SB_ERR_INVALID_ARG, "dt must be > 0");
-    mat = SB_MAT_CH_NOFLUX;
+    mat = bc == SB_BC_PERIODIC ? SB_MAT_CH_PERIODIC : SB_MAT_CH_NOFLUX;
     acoef = dt * coef;
   } else {
     return fail(SB_ERR_INVALID_ARG, "unknown stepper kind %d", kind);
@@ -404,6 +447,9 @@ int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, doub
                                        &st->fac);
   else if (P == 1)
     rc = sb_factor_shared_tri(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N, &st->fac);
+  else if (mat == SB_MAT_CH_PERIODIC)
+    rc = sb_factor_shared_penta_periodic(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N,
+                                         adiag.data() + 3 * N, adiag.data() + 4 * N, &st->fac);
   else
     rc = sb_factor_shared_penta(N, adiag.data(), adiag.data() + N, adiag.data() + 2 * N,
                                 adiag.data() + 3 * N, adiag.data() + 4 * N, &st->fac);
@@ -415,9 +461,10 @@ int sb_stepper_create(int kind, int scheme, int bc, int64_t N, double coef, doub
   std::vector<double> rows;
   if (kind == SB_STEP_CAHN_HILLIARD) {
     st->has_e = true;
-    rows.assign(3 * N, 0.0);  // dt * D2_N, cell-centred no-flux closure
+    rows.assign(3 * N, 0.0);  // dt * D2_N (cell-centred no-flux closure) or dt * D2_P
+    const bool per = bc == SB_BC_PERIODIC;
     for (int64_t i = 0; i < N; ++i) {
-      const bool first = (i == 0), last = (i == N - 1);
+      const bool first = (i == 0) && !per, last = (i == N - 1) && !per;
       rows[3 * i + 0] = first ? 0.0 : dt;
       rows[3 * i + 1] = dt * (-2.0 + (first ? 1.0 : 0.0) + (last ? 1.0 : 0.0));
       rows[3 * i + 2] = last ? 0.0 : dt;

@@ -23,11 +23,15 @@
 namespace sb {
 namespace {
 
+// Per-op length of a periodic factor's correction data (rank 1 or 2).
+__host__ __device__ constexpr int cyc_len(int rank, int N) { return rank == 1 ? 2 * N : rank == 2 ? 4 * N + 12 : 0; }
+
 // Single-factor kernel: persistent CTAs stage the coefficients once, then their
-// warps take tiles round-robin over the grid.  CYC: the periodic tridiagonal
-// matrix (section 3.3); its correction rows are staged after the coefficients.
+// warps take tiles round-robin over the grid.  CYC: periodic matrices (rank-1
+// tridiagonal of section 3.3, rank-2 cyclic pentadiagonal); the correction data is
+// staged after the coefficients.
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
-          bool CYC>
+          int CYC>
 __global__ void __launch_bounds__(512)
 sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld,
              const TI* rhs, TO* x, int64_t ntiles, const typename A::C* __restrict__ cyc,
@@ -37,7 +41,7 @@ sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t l
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cs = reinterpret_cast<C*>(smem_raw);
   stage(cs, coef, 2 * W * N);
-  if constexpr (CYC) stage(cs + 2 * W * N, cyc, 2 * N);
+  if constexpr (CYC) stage(cs + 2 * W * N, cyc, cyc_len(CYC, N));
   __syncthreads();
   const int nw = blockDim.x >> 5;
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
@@ -52,18 +56,23 @@ template <class A>
 struct CycData;
 template <>
 struct CycData<NativeArith<double>> {
-  static const double* rows(const sb_factor* f, int o) { return f->cyc64 ? f->cyc64 + 2 * f->N * o : nullptr; }
+  static const double* rows(const sb_factor* f, int o) {
+    return f->cyc64 ? f->cyc64 + cyc_len(f->periodic_rank, (int)f->N) * o : nullptr;
+  }
   static double coef(double v) { return v; }
 };
 template <>
 struct CycData<NativeArith<float>> {
-  static const float* rows(const sb_factor* f, int o) { return f->cyc32 ? f->cyc32 + 2 * f->N * o : nullptr; }
+  static const float* rows(const sb_factor* f, int o) {
+    return f->cyc32 ? f->cyc32 + cyc_len(f->periodic_rank, (int)f->N) * o : nullptr;
+  }
   static float coef(double v) { return (float)v; }
 };
 template <>
 struct CycData<DFArith> {
   static const df* rows(const sb_factor* f, int o) {
-    return f->cycdf ? reinterpret_cast<const df*>(f->cycdf) + 2 * f->N * o : nullptr;
+    return f->cycdf ? reinterpret_cast<const df*>(f->cycdf) + cyc_len(f->periodic_rank, (int)f->N) * o
+                    : nullptr;
   }
   static df coef(double v) {
     const float h = (float)v;
@@ -74,12 +83,12 @@ struct CycData<DFArith> {
 // ----------------------------------------------------------------- launching
 
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
-          bool CYC>
+          int CYC>
 int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
            int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
   using C = typename A::C;
   const int N = (int)f->N;
-  const size_t smem = ((size_t)2 * (P + 1) * N + (CYC ? (size_t)2 * N : 0)) * sizeof(C);
+  const size_t smem = ((size_t)2 * (P + 1) * N + (size_t)cyc_len(CYC, N)) * sizeof(C);
   if (smem > 227 * 1024)
     return fail(SB_ERR_UNSUPPORTED,
                 "N=%d: the shared factors (%zu B) exceed the shared memory of one CTA", N, smem);
@@ -103,7 +112,7 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   return cuda_check(cudaGetLastError(), "sweep kernel launch");
 }
 
-template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, bool CYC>
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int CYC>
 int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
                int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
   if (shape.spt == 2)
@@ -120,15 +129,19 @@ int dispatch_pb(const sb_factor* f, Op op, const typename A::C* base, const void
   if (f->P == 1) {
     if (f->periodic)
       return op == OP_PRIMAL
-                 ? launch_spt<A, 1, false, true, TI, TO, true>(f, c, rhs, x, M, ld, shape, stream, o)
-                 : launch_spt<A, 1, true, false, TI, TO, true>(f, c, rhs, x, M, ld, shape, stream, o);
+                 ? launch_spt<A, 1, false, true, TI, TO, 1>(f, c, rhs, x, M, ld, shape, stream, o)
+                 : launch_spt<A, 1, true, false, TI, TO, 1>(f, c, rhs, x, M, ld, shape, stream, o);
     return op == OP_PRIMAL
-               ? launch_spt<A, 1, false, true, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o)
-               : launch_spt<A, 1, true, false, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o);
+               ? launch_spt<A, 1, false, true, TI, TO, 0>(f, c, rhs, x, M, ld, shape, stream, o)
+               : launch_spt<A, 1, true, false, TI, TO, 0>(f, c, rhs, x, M, ld, shape, stream, o);
   }
+  if (f->periodic)
+    return op == OP_PRIMAL
+               ? launch_spt<A, 2, false, true, TI, TO, 2>(f, c, rhs, x, M, ld, shape, stream, o)
+               : launch_spt<A, 2, true, false, TI, TO, 2>(f, c, rhs, x, M, ld, shape, stream, o);
   return op == OP_PRIMAL
-             ? launch_spt<A, 2, false, true, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o)
-             : launch_spt<A, 2, true, false, TI, TO, false>(f, c, rhs, x, M, ld, shape, stream, o);
+             ? launch_spt<A, 2, false, true, TI, TO, 0>(f, c, rhs, x, M, ld, shape, stream, o)
+             : launch_spt<A, 2, true, false, TI, TO, 0>(f, c, rhs, x, M, ld, shape, stream, o);
 }
 
 }  // namespace

@@ -43,16 +43,20 @@ __device__ __forceinline__ void stage(C* dst, const C* __restrict__ src, int n) 
 }
 
 // Solves the tile `tile` (32 * SPT consecutive systems) with coefficient rows
-// fw (forward) and bw (backward) (with CYC, the periodic matrix of section 3.3:
-// rows cy = (w_i, -z_i) and scalars alpha, beta give the Sherman-Morrison
-// correction x = y - f z, f = beta (w . rhs + alpha y_{N-1}), applied as x is
-// written):
+// fw (forward) and bw (backward).  CYC = 1: the periodic tridiagonal matrix of
+// section 3.3: rows cy = (w_i, -z_i) and scalars alpha, beta give the
+// Sherman-Morrison correction x = y - f z, f = beta (w . rhs + alpha y_{N-1}),
+// applied as x is written.  CYC = 2: the cyclic pentadiagonal matrix (rank-2
+// correction): rows cy = (w0_i, w1_i, -z0_i, -z1_i) and, after the N rows, 12
+// scalars P, Q, S^{-1}; g = S^{-1} (P (y_0, y_1) + Q (y_{N-2}, y_{N-1})) with
+// y_0 = w0 . rhs and y_1 = w1 . rhs, x = y - z0 g_0 - z1 g_1; rows N-1 and N-2 are
+// written once g is known.
 //   forward  u_i = F0 r_i - F1 u_{i-1} - F2 u_{i-2}      (F0 == 1 when F_ONE)
 //   backward x_i = B0 u_i - B1 x_{i+1} - B2 x_{i+2}      (B0 == 1 when B_ONE)
 // The intermediate u is stored in place in x; SPT systems per thread (m and
 // m + 32, ...) interleave independent recurrences; R rows per prefetch batch.
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
-          bool CYC = false>
+          int CYC = 0>
 __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typename A::C* bw, int N,
                                            int64_t M, int64_t ld, const TI* rhs, TO* x,
                                            int64_t tile, const typename A::C* cy = nullptr,
@@ -77,9 +81,9 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
     };
 
     // ---- forward sweep
-    V u1[SPT], u2[SPT], dot[SPT];
+    V u1[SPT], u2[SPT], dot[SPT], dot1[SPT];
 #pragma unroll
-    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = dot[s] = A::zero();
+    for (int s = 0; s < SPT; ++s) u1[s] = u2[s] = dot[s] = dot1[s] = A::zero();
     TI va[R][SPT], vb[R][SPT];
     auto load_in = [&](TI (&buf)[R][SPT], int i0) {
 #pragma unroll
@@ -98,7 +102,11 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
           for (int s = 0; s < SPT; ++s) {
             const V in = Conv<A, TI>::in(buf[j][s]);
             const V u = A::template step<P, F_ONE>(c, in, u1[s], u2[s]);
-            if constexpr (CYC) dot[s] = A::fmac(cy[2 * i], in, dot[s]);
+            if constexpr (CYC == 1) dot[s] = A::fmac(cy[2 * i], in, dot[s]);
+            if constexpr (CYC == 2) {
+              dot[s] = A::fmac(cy[4 * i], in, dot[s]);
+              dot1[s] = A::fmac(cy[4 * i + 1], in, dot1[s]);
+            }
             if (ok[s]) *slot(i, s) = A::to_store(u);
             u2[s] = u1[s];
             u1[s] = u;
@@ -115,9 +123,9 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
     }
 
     // ---- backward sweep
-    V x1[SPT], x2[SPT], fc[SPT];
+    V x1[SPT], x2[SPT], fc[SPT], g1[SPT];
 #pragma unroll
-    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = fc[s] = A::zero();
+    for (int s = 0; s < SPT; ++s) x1[s] = x2[s] = fc[s] = g1[s] = A::zero();
     S sa[R][SPT], sb_[R][SPT];
     auto load_mid = [&](S (&buf)[R][SPT], int i0) {
 #pragma unroll
@@ -135,9 +143,30 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
 #pragma unroll
           for (int s = 0; s < SPT; ++s) {
             const V xi = A::template step<P, B_ONE>(c, A::from_store(buf[j][s]), x1[s], x2[s]);
-            if constexpr (CYC) {
+            if constexpr (CYC == 1) {
               if (i == N - 1) fc[s] = A::mulc(beta, A::fmac(alpha, xi, dot[s]));
               if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(A::fmac(cy[2 * i + 1], fc[s], xi)));
+            } else if constexpr (CYC == 2) {
+              if (i < N - 2) {
+                if (ok[s])
+                  st_stream(y + (int64_t)i * ld + 32 * s,
+                            Conv<A, TO>::out(A::fmac(cy[4 * i + 3], g1[s], A::fmac(cy[4 * i + 2], fc[s], xi))));
+              } else if (i == N - 2) {
+                // x1 holds y_{N-1}: g = S^{-1} (P (y_0, y_1) + Q (y_{N-2}, y_{N-1}))
+                const C* sc = cy + 4 * N;
+                const V yl = x1[s];
+                const V t0 = A::fmac(sc[0], dot[s], A::fmac(sc[1], dot1[s], A::fmac(sc[4], xi, A::mulc(sc[5], yl))));
+                const V t1 = A::fmac(sc[2], dot[s], A::fmac(sc[3], dot1[s], A::fmac(sc[6], xi, A::mulc(sc[7], yl))));
+                fc[s] = A::fmac(sc[8], t0, A::mulc(sc[9], t1));
+                g1[s] = A::fmac(sc[10], t0, A::mulc(sc[11], t1));
+                if (ok[s]) {
+                  const int j1 = N - 1;
+                  st_stream(y + (int64_t)j1 * ld + 32 * s,
+                            Conv<A, TO>::out(A::fmac(cy[4 * j1 + 3], g1[s], A::fmac(cy[4 * j1 + 2], fc[s], yl))));
+                  st_stream(y + (int64_t)i * ld + 32 * s,
+                            Conv<A, TO>::out(A::fmac(cy[4 * i + 3], g1[s], A::fmac(cy[4 * i + 2], fc[s], xi))));
+                }
+              }
             } else {
               if (ok[s]) st_stream(y + (int64_t)i * ld + 32 * s, Conv<A, TO>::out(xi));
             }

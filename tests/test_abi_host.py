@@ -133,6 +133,17 @@ def test_product_periodic_matrix_builder_matches_oracle(sb, N):
         sb.sb_build_matrix("diffusion_periodic", 2, 0.37)
 
 
+@pytest.mark.parametrize("N", [5, 6, 17, 256])
+def test_product_periodic_ch_matrix_builder_matches_oracle(sb, N):
+    from oracle import matrices
+    mine = sb.sb_build_matrix("ch_periodic", N, 0.21)
+    ref = matrices.ch_matrix_periodic(N, 0.21)
+    for u, v in zip(mine, ref):
+        assert np.allclose(u, v, rtol=0, atol=1e-15)
+    with pytest.raises(sb.SbError):
+        sb.sb_build_matrix("ch_periodic", 4, 0.21)
+
+
 def test_product_matrix_builder_rejects_bad_input(sb):
     with pytest.raises(sb.SbError):
         sb.sb_build_matrix(99, 8, 0.1)

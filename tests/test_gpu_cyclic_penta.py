@@ -1,0 +1,140 @@
+"""GPU parity of the cyclic pentadiagonal solve (rank-2 Sherman-Morrison-Woodbury)
+and of the periodic Cahn-Hilliard / hyperdiffusion steppers against the oracle on
+the same seeded inputs: A and A^T in native FP64, FP32, FP32 -> FP64 and
+double-float, both systems-per-thread shapes, ragged tiles and padding canaries,
+in place; the circulant's Fourier-mode decay; periodic CH over many steps with the
+mass of every system conserved.
+
+Tolerances: 1e-12 relative L2 per system (FP64; double-float single solves),
+2e-5 (FP32), 1e-10 for multi-step double-float runs (as for every stepper)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import banded, matrices, steppers
+from tests.gpu_util import lib_or_skip, relerr_per_system, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+CANARY = 4.25
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_or_skip()
+
+
+def random_cyclic(seed, N):
+    g = np.random.default_rng([seed, 5])
+    a, b, d, e = (g.uniform(-1, 1, N) for _ in range(4))
+    c = np.sign(g.uniform(-1, 1, N)) * (np.abs(a) + np.abs(b) + np.abs(d) + np.abs(e) + 0.5 + g.uniform(0, 1, N))
+    return a, b, c, d, e
+
+
+def oracle(diags, rhs, adjoint):
+    f = banded.penta_periodic_factor(*diags)
+    return (banded.penta_periodic_solve_adjoint if adjoint else banded.penta_periodic_solve)(f, rhs)
+
+
+@pytest.mark.parametrize("N,M", [(5, 7), (6, 33), (17, 64), (256, 1000), (1000, 131)])
+@pytest.mark.parametrize("mode", ["native64", "native32", "f32_to_f64", "df32"])
+@pytest.mark.parametrize("spt", [1, 2])
+def test_cyclic_penta_matches_oracle(env, N, M, mode, spt):
+    sb, torch = env
+    diags = random_cyclic(N, N)
+    fac = sb.sb_factor_shared_penta_periodic(*diags)
+    ld = M + 5
+    rt, xt, arith = {"native64": (np.float64, np.float64, "native"),
+                     "native32": (np.float32, np.float32, "native"),
+                     "f32_to_f64": (np.float32, np.float64, "native"),
+                     "df32": (np.float64, np.float64, "df32")}[mode]
+    codes = {np.float64: sb.SB_F64, np.float32: sb.SB_F32}
+    sb.sb_shape_set(fac, (128, 0, spt, 0), arith=arith, rhs_dtype=codes[rt], x_dtype=codes[xt])
+    rhs = synth.rhs_normal(seed=N + 2, N=N, M=M, ld=ld, pad_value=CANARY).astype(rt)
+    d = to_dev(rhs, torch)
+    x = torch.full((N, ld), CANARY, dtype=torch.float64 if xt == np.float64 else torch.float32, device="cuda")
+    tol = TOL32 if mode in ("native32", "f32_to_f64") else TOL64
+    for adjoint in (False, True):
+        sb.sb_solve_batched_ex(fac, d, x, transpose=adjoint, arith=arith, M=M)
+        torch.cuda.synchronize()
+        out = to_host(x).astype(np.float64)
+        err = np.max(relerr_per_system(out[:, :M], oracle(diags, rhs[:, :M].astype(np.float64), adjoint)))
+        assert err <= tol, (N, M, mode, spt, adjoint, err)
+        assert np.all(out[:, M:] == CANARY)
+
+
+def test_cyclic_penta_in_place_and_mode_decay(env):
+    sb, torch = env
+    N, s = 256, 0.37
+    fac = sb.sb_factor_shared_penta_periodic(*sb.sb_build_matrix("ch_periodic", N, s))
+    modes = [0, 1, 3, 64, 127, 128]
+    X = np.concatenate([synth.fourier_mode_block(N, modes, "cos"), synth.fourier_mode_block(N, modes, "sin")], axis=1)
+    lam = 1.0 + 16.0 * s * np.sin(np.pi * np.asarray(modes + modes) / N) ** 4
+    d = to_dev(X, torch)
+    sb.sb_solve_batched(fac, d)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_host(d) - X / lam[None, :])) <= 1e-13
+
+
+def oracle_run(kind, scheme, N, coef, dt, C, nsteps):
+    C = C.copy()
+    if kind == "cahn_hilliard":
+        A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, dt * coef))
+        for _ in range(nsteps):
+            C = steppers.ch_step_periodic(A, C, dt)
+    else:
+        A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, coef))
+        for _ in range(nsteps):
+            C = A.solve(C if scheme == "be" else C - coef * matrices.apply_penta_periodic(*matrices.d4_periodic(N), C))
+    return C
+
+
+STEP_CASES = [
+    ("cahn_hilliard", "be", synth.CH_GAMMA_GRID, synth.CH_DT_GRID, 0.1),
+    ("cahn_hilliard", "be", 1.0, 0.05, 0.9),  # strongly nonlinear
+    ("hyperdiffusion", "be", 0.25, 0.0, 1.0),
+    ("hyperdiffusion", "cn", 0.3, 0.0, 1.0),
+]
+
+
+@pytest.mark.parametrize("mode", ["graph", "direct", "unfused"])
+@pytest.mark.parametrize("arith", ["native", "df32"])
+@pytest.mark.parametrize("kind,scheme,coef,dt,amp", STEP_CASES)
+@pytest.mark.parametrize("N", [5, 6, 37])
+def test_periodic_stepper_matches_oracle(env, kind, scheme, coef, dt, amp, N, arith, mode):
+    sb, torch = env
+    M, ld, nsteps = 200, 203, 70
+    st = sb.sb_stepper_create(kind, scheme, "periodic", N, coef, dt)
+    C0 = synth.rhs_uniform(seed=N + 7, N=N, M=M, ld=ld, lo=-amp, hi=amp, pad_value=2.5)
+    d = to_dev(C0, torch)
+    work = torch.empty_like(d) if mode == "unfused" else None
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        sb.sb_stepper_run(st, d, nsteps, arith=arith, mode=mode, work=work, M=M, stream=stream)
+    torch.cuda.synchronize()
+    out = to_host(d)
+    ref = oracle_run(kind, scheme, N, coef, dt, C0[:, :M], nsteps)
+    floor = 1e-26 if arith == "df32" else 0.0
+    err = np.linalg.norm(out[:, :M] - ref, axis=0) / np.maximum(np.linalg.norm(ref, axis=0), floor)
+    assert np.max(err) <= (1e-12 if arith == "native" else 1e-10), (kind, scheme, N, arith, mode, np.max(err))
+    assert np.all(out[:, M:] == 2.5)
+
+
+def test_periodic_ch_workload_sampled_and_mass(env):
+    """Periodic CH, N = 256, 2^16 simulations, 500 steps (fused + graph, FP64):
+    256 sampled systems against the oracle, the mass of every system conserved."""
+    sb, torch = env
+    N, M, steps = 256, 1 << 16, 500
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, synth.CH_GAMMA_GRID, synth.CH_DT_GRID)
+    C = synth.torch_uniform(4, N, M, -0.1, 0.1, torch.float64, "cuda")
+    mass0 = C.sum(dim=0).clone()
+    cols = torch.as_tensor(np.linspace(0, M - 1, 256).astype(np.int64), device="cuda")
+    C0s = to_host(C[:, cols])
+    sb.sb_stepper_run(st, C, steps)
+    torch.cuda.synchronize()
+    ref = oracle_run("cahn_hilliard", "be", N, synth.CH_GAMMA_GRID, synth.CH_DT_GRID, C0s, steps)
+    assert np.max(relerr_per_system(to_host(C[:, cols]), ref)) <= 1e-12
+    assert float((C.sum(dim=0) - mass0).abs().max()) <= 1e-12 * N
