@@ -345,6 +345,40 @@ def extra_periodic_cn(sb, torch, stream):
     return out
 
 
+def extra_coarsening(sb, torch, stream):
+    """Section 5.3's batched coarsening study with the paper's periodic ends:
+    L = 2 pi, N = 256 (dx = 2 pi / 256), gamma = 0.01, dt = 0.1 dx, T = 100 (40 744
+    steps), C(x, 0) ~ U[-0.1, 0.1]; here 2^16 simulations (the paper: 2^20).  ell(t)
+    is recorded after every step; reported: the run time and the correlation
+    coefficient r of the least-squares line ell(t) ~ log t (the paper: r = 0.9989)."""
+    import math
+    import numpy as np
+    import synth
+    N, M = 256, 1 << 16
+    dx = 2.0 * math.pi / N
+    gamma_grid = 0.01 / dx ** 2
+    dt_phys = 0.1 * dx
+    dt_grid = dt_phys / dx ** 2
+    steps = int(round(100.0 / dt_phys))
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, gamma_grid, dt_grid)
+    C = synth.torch_uniform(4, N, M, -0.1, 0.1, torch.float64, "cuda")
+    ell = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    work = torch.empty(M + 256, dtype=torch.float64, device="cuda")
+    ms = _events_ms(lambda: sb.sb_stepper_run_coarsening(st, C, steps, ell, work), 1,
+                    torch.cuda.current_stream())
+    e = ell.cpu().numpy()
+    t = dt_phys * np.arange(1, steps + 1)
+    out = {"workload": f"periodic CH, L=2pi, N=256, gamma=0.01, dt=0.1dx, T=100 ({steps} steps), "
+                       f"M=2^16, C0~U[-0.1,0.1], FP64",
+           "s_total": ms / 1e3, "ms_per_step": ms / steps, "finite": bool(np.all(np.isfinite(e))),
+           "ell_at_t": {str(tt): float(e[int(round(tt / dt_phys)) - 1]) for tt in (1, 10, 50, 100)}}
+    for lo in (1.0, 10.0):
+        sel = t >= lo
+        out[f"r_log_fit_t{int(lo)}_100"] = float(np.corrcoef(np.log(t[sel]), e[sel])[0, 1])
+    out["paper_r_2pi"] = 0.9989
+    return out
+
+
 def extra_rollout(sb, torch, stream):
     """Adjoint rollout, N=512, 2^16 systems, 200 steps, checkpoints every 20 (CH
     and diffusion, FP64): forward and backward step rates against the plain
@@ -507,7 +541,7 @@ def run_ours(args):
     if not args.no_extras:
         for name, fn in (("tri_latency", extra_tri_latency), ("multigroup_refine", extra_multigroup),
                          ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout),
-                         ("paper_table1_periodic_cn", extra_periodic_cn)):
+                         ("paper_table1_periodic_cn", extra_periodic_cn), ("coarsening", extra_coarsening)):
             try:
                 extras[name] = fn(sb, torch, stream)
             except Exception as exc:  # report, do not hide, a failing extra

@@ -429,6 +429,23 @@ int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arit
                    int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream);
 
 /*
+ * sb_stepper_run_coarsening -- nsteps fused Cahn-Hilliard steps (as
+ * sb_stepper_run with SB_RUN_DIRECT) that also record section 5.3's typical domain
+ * size after every step: ell[n] = mean over the M systems of 1 / (1 - <C^2>), with
+ * <C^2> the mean of C_i^2 over the N grid points (the periodic rectangle rule for
+ * (1/L) int C^2 dx) of the state after step n + 1.  Each system's value is formed in
+ * the step's backward sweep; the mean is a fixed-order reduction, so ell is the
+ * same on every run.
+ *   st     a SB_STEP_CAHN_HILLIARD stepper (SB_BC_NOFLUX or SB_BC_PERIODIC).
+ *   ell    device array of nsteps doubles.
+ *   work   device workspace of (M + 256) doubles.
+ * Other arguments as for sb_stepper_run.  SB_ERR_UNSUPPORTED for other stepper kinds.
+ */
+int sb_stepper_run_coarsening(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+                              int64_t nsteps, double* ell, void* work, size_t work_bytes,
+                              void* stream);
+
+/*
  * Differentiable rollouts (S8 + S9 of the hot path; no counterpart in the paper,
  * which only runs forward).  For a backward-Euler diffusion / hyperdiffusion or a
  * Cahn-Hilliard stepper, the rollout x_{n+1} = A(p)^{-1} F(x_n), n < nsteps, with p

@@ -102,6 +102,8 @@ SIGNATURES = {
     "sb_stepper_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "sb_stepper_run": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, ctypes.c_int, _vp,
                                       ctypes.c_size_t, _vp]),
+    "sb_stepper_run_coarsening": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, _vp, _vp,
+                                                 ctypes.c_size_t, _vp]),
     "sb_device_timeouts": (ctypes.c_int, [ctypes.c_int, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
@@ -459,6 +461,18 @@ def sb_stepper_run(st: Stepper, state, nsteps, arith="native", mode="graph", wor
                                 RUN_MODES[mode] if isinstance(mode, str) else int(mode), wptr or None,
                                 wbytes, _stream_handle(stream)))
     return state
+
+
+def sb_stepper_run_coarsening(st: Stepper, state, nsteps, ell, work, arith="native", M=None, ld=None,
+                              stream=None):
+    """Advance a Cahn-Hilliard `state` by nsteps fused steps and write the mean
+    coarsening length 1/(1 - <C^2>) after each step into `ell` (nsteps FP64 values
+    on the device); `work` holds M + 256 doubles."""
+    M, ld = _batch_shape(state, st.N, M, ld)
+    _check(lib().sb_stepper_run_coarsening(st.handle, _dev_ptr(state), M, ld, _arith_code(arith),
+                                           int(nsteps), _dev_ptr(ell), _dev_ptr(work), _nbytes(work),
+                                           _stream_handle(stream)))
+    return ell
 
 
 def sb_rollout_workspace_bytes(st: Stepper, M, nsteps, ckpt_every, ld=None):

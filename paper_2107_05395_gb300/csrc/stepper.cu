@@ -49,11 +49,14 @@ __host__ __device__ constexpr int step_cyc_len(int rank, int N) {
   return rank == 1 ? 2 * N : rank == 2 ? 4 * N + 12 : 0;
 }
 
-template <class A, int P, int NB, bool HAS_E, int R, int CYC>
+// STATS: each system's new state also gives ell_m = 1 / (1 - <C^2>), <C^2> the mean
+// of C_i^2 over its N rows (section 5.3's coarsening length), written to ellm[m].
+template <class A, int P, int NB, bool HAS_E, int R, int CYC, bool STATS = false>
 __global__ void __launch_bounds__(512)
 fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
                   int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles,
-                  const typename A::C* __restrict__ cyc, typename A::C alpha, typename A::C beta) {
+                  const typename A::C* __restrict__ cyc, typename A::C alpha, typename A::C beta,
+                  double* __restrict__ ellm = nullptr) {
   using V = typename A::V;
   using C = typename A::C;
   using S = typename A::S;
@@ -181,6 +184,12 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
 
     // backward sweep (B0 == 1 for the primal factors)
     V x1 = A::zero(), x2 = A::zero(), fc = A::zero(), g1 = A::zero();
+    double sq = 0.0;
+    auto emit = [&](int row, V v) {
+      const double o = StConv<A, double>::out(v);
+      y[(int64_t)row * ld] = o;
+      if constexpr (STATS) sq = fma(o, o, sq);
+    };
     S sa[R], sb_[R];
     auto load_mid = [&](S (&buf)[R], int i0) {
 #pragma unroll
@@ -195,10 +204,10 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
           const V xi = A::template step<P, true>(bw + W * i, A::from_store(buf[j]), x1, x2);
           if constexpr (CYC == 1) {
             if (i == N - 1) fc = A::mulc(beta, A::fmac(alpha, xi, dot));
-            y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[2 * i + 1], fc, xi));
+            emit(i, A::fmac(cy[2 * i + 1], fc, xi));
           } else if constexpr (CYC == 2) {
             if (i < N - 2) {
-              y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
+              emit(i, A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
             } else if (i == N - 2) {  // x1 holds y_{N-1}
               const C* sc = cy + 4 * N;
               const V t0 = A::fmac(sc[0], dot, A::fmac(sc[1], dot1, A::fmac(sc[4], xi, A::mulc(sc[5], x1))));
@@ -206,11 +215,11 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
               fc = A::fmac(sc[8], t0, A::mulc(sc[9], t1));
               g1 = A::fmac(sc[10], t0, A::mulc(sc[11], t1));
               const int j1 = N - 1;
-              y[(int64_t)j1 * ld] = StConv<A, double>::out(A::fmac(cy[4 * j1 + 3], g1, A::fmac(cy[4 * j1 + 2], fc, x1)));
-              y[(int64_t)i * ld] = StConv<A, double>::out(A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
+              emit(j1, A::fmac(cy[4 * j1 + 3], g1, A::fmac(cy[4 * j1 + 2], fc, x1)));
+              emit(i, A::fmac(cy[4 * i + 3], g1, A::fmac(cy[4 * i + 2], fc, xi)));
             }
           } else {
-            y[(int64_t)i * ld] = StConv<A, double>::out(xi);
+            emit(i, xi);
           }
           x2 = x1;
           x1 = xi;
@@ -224,7 +233,40 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
       load_mid(sa, i0 - 2 * R);
       bwd(sb_, i0 - R);
     }
+    if constexpr (STATS) ellm[m] = 1.0 / (1.0 - sq / (double)N);
   }
+}
+
+// Fixed-shape deterministic mean of the per-system values: kMeanBlocks partial sums
+// over fixed index ranges (fixed strided order, fixed shared-memory tree), then one
+// block sums the partials and scales by 1/M.
+constexpr int kMeanBlocks = 256;
+constexpr int kMeanThreads = 256;
+
+__global__ void __launch_bounds__(kMeanThreads) mean_partials(const double* v, int64_t n, double* part) {
+  __shared__ double sh[kMeanThreads];
+  const int64_t chunk = (n + kMeanBlocks - 1) / kMeanBlocks;
+  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kMeanThreads) acc += v[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kMeanThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kMeanThreads) mean_final(const double* part, int64_t n, double* out) {
+  __shared__ double sh[kMeanThreads];
+  sh[threadIdx.x] = (threadIdx.x < kMeanBlocks) ? part[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int w = kMeanThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0] / (double)n;
 }
 
 // Unfused right-hand side (the paper's separate stencil pass): f = B C + E phi(C);
@@ -288,9 +330,10 @@ struct StepCyc<DFArith> {
   }
 };
 
-template <class A, int P, int NB, bool HAS_E, int CYC>
+template <class A, int P, int NB, bool HAS_E, int CYC, bool STATS = false>
 int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
-                 const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream) {
+                 const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream,
+                 double* ellm = nullptr) {
   const sb_factor* f = st->fac;
   const int N = (int)f->N;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
@@ -298,7 +341,7 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
       ((size_t)2 * (P + 1) * N + (size_t)RW * N + (size_t)step_cyc_len(CYC, N)) * sizeof(typename A::C);
   if (smem > 227 * 1024)
     return fail(SB_ERR_UNSUPPORTED, "N=%d too large for the fused step's shared memory", N);
-  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC>;
+  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC, STATS>;
   const int threads = 256;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, int> occ;
@@ -321,7 +364,7 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
   const typename A::C* cy = CYC ? StepCyc<A>::rows(f) : nullptr;  // primal rows (op 0)
   k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles, cy,
                                               StepCyc<A>::coef(CYC ? f->cyc_alpha[0] : 0.0),
-                                              StepCyc<A>::coef(CYC ? f->cyc_beta[0] : 0.0));
+                                              StepCyc<A>::coef(CYC ? f->cyc_beta[0] : 0.0), ellm);
   return cuda_check(cudaGetLastError(), "fused step launch");
 }
 
@@ -353,6 +396,16 @@ int one_step(const sb_stepper* st, const typename A::C* coef, const typename A::
                        : launch_fused<A, 2, 0, false, 2>(st, coef, rc, src, state, M, ld, stream);
   return st->NB == 5 ? launch_fused<A, 2, 5, false, 0>(st, coef, rc, src, state, M, ld, stream)
                      : launch_fused<A, 2, 0, false, 0>(st, coef, rc, src, state, M, ld, stream);
+}
+
+// A fused Cahn-Hilliard step that also writes each system's coarsening length.
+template <class A>
+int one_step_stats(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
+                   double* state, int64_t M, int64_t ld, cudaStream_t stream, double* ellm) {
+  if (!st->has_e) return fail(SB_ERR_UNSUPPORTED, "the coarsening statistic needs a Cahn-Hilliard stepper");
+  return st->fac->periodic
+             ? launch_fused<A, 2, 0, true, 2, true>(st, coef, rc, state, state, M, ld, stream, ellm)
+             : launch_fused<A, 2, 0, true, 0, true>(st, coef, rc, state, state, M, ld, stream, ellm);
 }
 
 template <class A>
@@ -519,6 +572,47 @@ void sb_stepper_destroy(sb_stepper* st) {
 }
 
 const sb_factor* sb_stepper_factor(const sb_stepper* st) { return st ? st->fac : nullptr; }
+
+int sb_stepper_run_coarsening(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
+                              int64_t nsteps, double* ell, void* work, size_t work_bytes,
+                              void* stream) {
+  clear_error();
+  if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
+  if (st->kind != SB_STEP_CAHN_HILLIARD)
+    return fail(SB_ERR_UNSUPPORTED, "the coarsening statistic needs a Cahn-Hilliard stepper");
+  if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode %d", (int)arith);
+  const sb_factor* f = st->fac;
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  if (M < 1 || ld < M) return fail(SB_ERR_INVALID_ARG, "need M >= 1 and ld >= M");
+  if (nsteps == 0) return SB_OK;
+  const size_t bytes = (size_t)((f->N - 1) * ld + M) * sizeof(double);
+  SB_TRY(check_device_range(state, bytes, sizeof(double), f->device, "state"));
+  SB_TRY(check_device_range(ell, (size_t)nsteps * sizeof(double), sizeof(double), f->device, "ell"));
+  const size_t need = ((size_t)M + kMeanBlocks) * sizeof(double);
+  if (work == nullptr || work_bytes < need)
+    return fail(SB_ERR_INVALID_ARG, "the coarsening run needs a workspace of %zu bytes", need);
+  SB_TRY(check_device_range(work, need, sizeof(double), f->device, "work"));
+  SB_TRY(check_alias(state, bytes, work, need, "state", "work"));
+  SB_TRY(check_alias(ell, (size_t)nsteps * sizeof(double), work, need, "ell", "work"));
+  SB_TRY(check_alias(ell, (size_t)nsteps * sizeof(double), state, bytes, "ell", "state"));
+  double* ellm = static_cast<double*>(work);
+  double* part = ellm + M;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    if (arith == SB_ARITH_DF32)
+      SB_TRY(one_step_stats<DFArith>(st, reinterpret_cast<const df*>(f->coefdf),
+                                     reinterpret_cast<const df*>(st->rdf), state, M, ld, s, ellm));
+    else
+      SB_TRY(one_step_stats<NativeArith<double>>(st, f->coef64, st->r64, state, M, ld, s, ellm));
+    mean_partials<<<kMeanBlocks, kMeanThreads, 0, s>>>(ellm, M, part);
+    mean_final<<<1, kMeanThreads, 0, s>>>(part, M, ell + n);
+    SB_CUDA(cudaGetLastError());
+  }
+  return SB_OK;
+}
 
 int sb_stepper_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes) {
   clear_error();

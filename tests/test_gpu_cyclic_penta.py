@@ -138,3 +138,72 @@ def test_periodic_ch_workload_sampled_and_mass(env):
     ref = oracle_run("cahn_hilliard", "be", N, synth.CH_GAMMA_GRID, synth.CH_DT_GRID, C0s, steps)
     assert np.max(relerr_per_system(to_host(C[:, cols]), ref)) <= 1e-12
     assert float((C.sum(dim=0) - mass0).abs().max()) <= 1e-12 * N
+
+
+@pytest.mark.parametrize("bc", ["periodic", "noflux"])
+@pytest.mark.parametrize("arith", ["native", "df32"])
+def test_coarsening_length_matches_oracle(env, bc, arith):
+    """Section 5.3's ell(t) = mean over systems of 1/(1 - <C^2>) after every step,
+    against the oracle's steps and definition; the same bits on a second run."""
+    sb, torch = env
+    N, M, steps = 64, 300, 100
+    gamma, dt = 0.5, 0.05  # ell grows from 1.08 to 1.33 over the run
+    st = sb.sb_stepper_create("cahn_hilliard", "be", bc, N, gamma, dt)
+    C0 = synth.rhs_uniform(seed=21, N=N, M=M, lo=-0.5, hi=0.5)
+    ells = []
+    for _ in range(2):
+        d = to_dev(C0, torch)
+        ell = torch.zeros(steps, dtype=torch.float64, device="cuda")
+        work = torch.empty(M + 256, dtype=torch.float64, device="cuda")
+        sb.sb_stepper_run_coarsening(st, d, steps, ell, work, arith=arith)
+        torch.cuda.synchronize()
+        ells.append(to_host(ell).copy())
+    assert np.array_equal(ells[0], ells[1])
+    if bc == "periodic":
+        A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, dt * gamma))
+        step = lambda C: steppers.ch_step_periodic(A, C, dt)
+    else:
+        A = steppers.SharedPenta(*matrices.ch_matrix(N, dt * gamma))
+        step = lambda C: steppers.ch_step(A, C, dt)
+    C = C0.copy()
+    ref = []
+    for _ in range(steps):
+        C = step(C)
+        ref.append(steppers.coarsening_length(C))
+    ref = np.asarray(ref)
+    assert ref[-1] > ref[0] * 1.05  # the statistic moves over the run
+    assert np.max(np.abs(ells[0] - ref) / ref) <= (1e-12 if arith == "native" else 1e-10)
+    assert np.max(relerr_per_system(to_host(d), C)) <= (1e-12 if arith == "native" else 1e-10)
+
+
+def test_coarsening_run_with_the_papers_parameters_stays_finite(env):
+    """Section 5.3's parameters (L = 2 pi, N = 256, gamma = 0.01, dt = 0.1 dx) for
+    2000 steps on 512 simulations: the semi-implicit scheme stays finite, mass is
+    conserved, and ell grows; 16 sampled systems match the oracle."""
+    import math
+    sb, torch = env
+    N, M, steps = 256, 512, 2000
+    dx = 2.0 * math.pi / N
+    g, dt = 0.01 / dx ** 2, 0.1 * dx / dx ** 2
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, g, dt)
+    C0 = synth.rhs_uniform(seed=4, N=N, M=M, lo=-0.1, hi=0.1)
+    d = to_dev(C0, torch)
+    ell = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    work = torch.empty(M + 256, dtype=torch.float64, device="cuda")
+    sb.sb_stepper_run_coarsening(st, d, steps, ell, work)
+    torch.cuda.synchronize()
+    e = to_host(ell)
+    out = to_host(d)
+    assert np.all(np.isfinite(e)) and np.all(np.isfinite(out))
+    # sigma = 67.6 amplifies rounding: the FP64 oracle itself drifts 5.4e-10 in mass
+    # over these 2000 steps (16 systems), so roundoff here is held to 2e-9
+    assert np.max(np.abs(out.sum(axis=0) - C0.sum(axis=0))) <= 2e-9
+    assert e[-1] > e[0]
+    A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, dt * g))
+    C = C0[:, :16].copy()
+    for _ in range(steps):
+        C = steppers.ch_step_periodic(A, C, dt)
+    # each step's solve rounds at cond(A) ~ 1 + 16 sigma = 1083 (about 1e-13), and
+    # the two sides round differently for 2000 steps of phase separation, so the
+    # comparison is held to 1e-9 (the 70- and 500-step runs above hold 1e-12)
+    assert np.max(relerr_per_system(out[:, :16], C)) <= 1e-9
