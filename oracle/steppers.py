@@ -19,6 +19,7 @@ __all__ = [
     "hyper_be_step", "hyper_cn_rhs",
     "ch_rhs", "ch_step", "solve_fp32_rhs",
     "SharedPentaPeriodic", "ch_rhs_periodic", "ch_step_periodic", "coarsening_length",
+    "convergence_error",
 ]
 
 
@@ -167,6 +168,17 @@ def coarsening_length(C):
     averaged over the simulations (the columns)."""
     C = np.asarray(C, dtype=np.float64)
     return float(np.mean(1.0 / (1.0 - np.mean(C * C, axis=0))))
+
+
+def convergence_error(C_half, C_full):
+    """E_N of the convergence study (section 5.2, Table 3) between the solution on N/2
+    points and the one on N points of the same periodic grid family x_i = i L / N:
+    the mean over the N/2 shared points of |C^(N/2)_i - C^(N)_(2i)|.  The paper does
+    not define E_N; this reading reproduces its printed values."""
+    C_half = np.asarray(C_half, dtype=np.float64)
+    C_full = np.asarray(C_full, dtype=np.float64)
+    assert C_full.shape[0] == 2 * C_half.shape[0]
+    return float(np.mean(np.abs(C_half - C_full[::2])))
 
 
 def solve_fp32_rhs(A, b32):

@@ -34,6 +34,7 @@ __all__ = [
     "sine_mode_block",
     "cosine_mode_block",
     "fourier_mode_block",
+    "ch_convergence_case",
     "torch_uniform",
     "torch_normal",
 ]
@@ -52,7 +53,23 @@ WORKLOADS = {
                           steps=2000, seed=4, amp=0.1),
     "adjoint_rollout": dict(N=512, M=1 << 16, steps=200, ckpt_every=20, r=0.5,
                             gamma=CH_GAMMA_GRID, dt=CH_DT_GRID, seed=5),
+    # convergence study of the periodic CH scheme (section 5.2): L = 2 pi, gamma = 0.01,
+    # dt = 0.1 dx, C(x, 0) = eps cos(5 x); the final time is not printed (T = 20 read)
+    "ch_convergence": dict(N=(64, 128, 256, 512, 1024, 2048, 4096, 8192), gamma=0.01,
+                           eps=1e-6, k=5, dt_over_dx=0.1, T=20.0),
 }
+
+
+def ch_convergence_case(N: int):
+    """Grid-unit parameters of the convergence study at N points on [0, 2 pi):
+    (gamma' = gamma / dx^2, dt' = dt / dx^2, steps = ceil(T / dt), physical dt, C0 of
+    shape (N, 1) = eps cos(5 x_i) with x_i = i dx)."""
+    w = WORKLOADS["ch_convergence"]
+    dx = 2.0 * math.pi / N
+    dt = w["dt_over_dx"] * dx
+    steps = int(math.ceil(w["T"] / dt))
+    C0 = w["eps"] * fourier_mode_block(N, [w["k"]], "cos")
+    return w["gamma"] / dx ** 2, dt / dx ** 2, steps, dt, C0
 
 
 def group_split(total: int, ratio, N) -> tuple:
