@@ -16,12 +16,16 @@ Contents, each function citing the passage it follows:
                    (sections 3.2, 4.2, 5.1) with Dirichlet / hinged / truncated /
                    no-flux closures.
 * ``steppers``  -- backward-Euler and Crank-Nicolson steps, the semi-implicit
-                   Cahn-Hilliard step (section 5.1), the FP64 reference for FP32
-                   right-hand sides.
+                   Cahn-Hilliard step (section 5.1, no-flux and periodic), the
+                   travelling-wave forced CH step (section 6.1), the coarsening
+                   length (section 5.3), the convergence-study error (Table 3), the
+                   FP64 reference for FP32 right-hand sides.
+* ``advection`` -- the fifth-order Hamilton-Jacobi WENO derivative of the forced
+                   scheme's advection term (section 6.1).
 * ``rollout``   -- discrete adjoint of an implicit rollout (no paper counterpart).
 
 Parity pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense LAPACK solves, exact rational elimination, closed-form eigenmode
 decay factors, conservation laws, the adjoint identity and finite differences.
 """
-from . import banded, matrices, rollout, steppers  # noqa: F401
+from . import advection, banded, matrices, rollout, steppers  # noqa: F401

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import banded, matrices
+from . import advection, banded, matrices
 
 __all__ = [
     "SharedTri", "SharedPenta",
@@ -19,7 +19,7 @@ __all__ = [
     "hyper_be_step", "hyper_cn_rhs",
     "ch_rhs", "ch_step", "solve_fp32_rhs",
     "SharedPentaPeriodic", "ch_rhs_periodic", "ch_step_periodic", "coarsening_length",
-    "convergence_error",
+    "convergence_error", "forced_ch_rhs_periodic", "forced_ch_step_periodic",
 ]
 
 
@@ -168,6 +168,29 @@ def coarsening_length(C):
     averaged over the simulations (the columns)."""
     C = np.asarray(C, dtype=np.float64)
     return float(np.mean(1.0 / (1.0 - np.mean(C * C, axis=0))))
+
+
+def forced_ch_rhs_periodic(C, alpha, beta, amp, profile):
+    """Right-hand side of the travelling-wave forced Cahn-Hilliard scheme (section
+    6.1) in grid units, periodic ends:
+        f = C^n + alpha D2_P (C^3 - C)^n + beta W(C^n) + amp_m g_i,
+    with W the fifth-order Hamilton-Jacobi WENO derivative, left-biased for
+    beta > 0 and right-biased for beta < 0 (the forcing wave's direction of travel),
+    beta = dt v / dx, g_i the forcing profile (the paper: dt k cos(k eta_i)) and
+    amp_m the amplitude of system m (the paper: f_0, one value per simulation)."""
+    C = np.asarray(C, dtype=np.float64)
+    f = ch_rhs_periodic(C, alpha)
+    if beta != 0.0:
+        f = f + beta * advection.weno5_derivative(C, -1 if beta > 0 else +1)
+    g = np.asarray(profile, dtype=np.float64)[:, None]
+    a = np.asarray(amp, dtype=np.float64)[None, :]
+    return f + a * g
+
+
+def forced_ch_step_periodic(A: SharedPentaPeriodic, C, alpha, beta, amp, profile):
+    """One semi-implicit forced CH step: (I + sigma D4_P) C^{n+1} =
+    forced_ch_rhs_periodic(C^n)."""
+    return A.solve(forced_ch_rhs_periodic(C, alpha, beta, amp, profile))
 
 
 def convergence_error(C_half, C_full):

@@ -35,6 +35,7 @@ __all__ = [
     "cosine_mode_block",
     "fourier_mode_block",
     "ch_convergence_case",
+    "forced_ch_convergence_case",
     "torch_uniform",
     "torch_normal",
 ]
@@ -57,7 +58,26 @@ WORKLOADS = {
     # dt = 0.1 dx, C(x, 0) = eps cos(5 x); the final time is not printed (T = 20 read)
     "ch_convergence": dict(N=(64, 128, 256, 512, 1024, 2048, 4096, 8192), gamma=0.01,
                            eps=1e-6, k=5, dt_over_dx=0.1, T=20.0),
+    # the same study for the travelling-wave forced CH scheme (section 6.1): forcing
+    # f0 k cos(k eta) with k = 1, f0 = 1, wave speed v = 0.5
+    "forced_ch_convergence": dict(N=(128, 256, 512, 1024, 2048, 4096), gamma=0.01, eps=1e-6,
+                                  k_init=5, dt_over_dx=0.1, T=20.0, k=1.0, f0=1.0, v=0.5),
+    # the flow-pattern batch of section 6.3: N = 512 on L = 2 pi, a 768 x 768 grid of
+    # (f0 in [0, 2], <C> in [0, 1.5]) = 589 824 simulations, C0 = <C> + U[-0.1, 0.1]
+    "forced_ch_map": dict(N=512, side=768, f0=(0.0, 2.0), mean=(0.0, 1.5), k=1.0, v=0.5,
+                          gamma=0.01, dt_over_dx=0.1, T=50.0, seed=6, amp=0.1),
 }
+
+
+def forced_ch_convergence_case(N: int):
+    """As ch_convergence_case, for the forced study's parameters (gamma' = gamma/dx^2,
+    dt' = dt/dx^2, steps = ceil(T/dt), physical dt, C0 = eps cos(5 x_i))."""
+    w = WORKLOADS["forced_ch_convergence"]
+    dx = 2.0 * math.pi / N
+    dt = w["dt_over_dx"] * dx
+    steps = int(math.ceil(w["T"] / dt))
+    C0 = w["eps"] * fourier_mode_block(N, [w["k_init"]], "cos")
+    return w["gamma"] / dx ** 2, dt / dx ** 2, steps, dt, C0
 
 
 def ch_convergence_case(N: int):
