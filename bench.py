@@ -7,6 +7,7 @@ once before timing (the paper times only the solve loop, section 3.4).  The
 inputs (2 x 512 MiB) exceed the 126 MiB L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--extras a,b] [--coarsening-systems M] [--table3-max-n N]
 Under torchrun (N > 1) each rank solves its own batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 
@@ -42,6 +43,8 @@ SM_COUNT = 152
 SM_MAX_GHZ = 2.07
 # FP64 FMA issue rate of GB300: 2 per clock per SM (nominal 1.25 TFLOP/s); peak in TFLOP/s.
 FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * SM_MAX_GHZ / 1e3
+# sizes of the paper-workload extras (set from the command line)
+OPTIONS = {"extras": [], "coarsening_systems": 1 << 16, "table3_max_n": 1024}
 
 
 def measured_peaks():
@@ -346,36 +349,241 @@ def extra_periodic_cn(sb, torch, stream):
 
 
 def extra_coarsening(sb, torch, stream):
-    """Section 5.3's batched coarsening study with the paper's periodic ends:
-    L = 2 pi, N = 256 (dx = 2 pi / 256), gamma = 0.01, dt = 0.1 dx, T = 100 (40 744
-    steps), C(x, 0) ~ U[-0.1, 0.1]; here 2^16 simulations (the paper: 2^20).  ell(t)
-    is recorded after every step; reported: the run time and the correlation
-    coefficient r of the least-squares line ell(t) ~ log t (the paper: r = 0.9989)."""
+    """Section 5.3's batched coarsening study with the paper's periodic ends, on both
+    of its domains: L = 2 pi (N = 256) and L = 4 pi (N = 512), dx = 2 pi / 256,
+    gamma = 0.01, dt = 0.1 dx, T = 100 (40 744 steps), C(x, 0) ~ U[-0.1, 0.1];
+    OPTIONS["coarsening_systems"] simulations (the paper: 2^20).  ell(t) is recorded
+    after every step; reported: the run time and the correlation coefficient r of
+    the least-squares line ell(t) ~ log t (the paper: r = 0.9989 and 0.9996)."""
     import math
     import numpy as np
     import synth
-    N, M = 256, 1 << 16
-    dx = 2.0 * math.pi / N
+    M = OPTIONS["coarsening_systems"]
+    dx = 2.0 * math.pi / 256
     gamma_grid = 0.01 / dx ** 2
     dt_phys = 0.1 * dx
     dt_grid = dt_phys / dx ** 2
     steps = int(round(100.0 / dt_phys))
-    st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, gamma_grid, dt_grid)
-    C = synth.torch_uniform(4, N, M, -0.1, 0.1, torch.float64, "cuda")
-    ell = torch.zeros(steps, dtype=torch.float64, device="cuda")
-    work = torch.empty(M + 256, dtype=torch.float64, device="cuda")
-    ms = _events_ms(lambda: sb.sb_stepper_run_coarsening(st, C, steps, ell, work), 1,
-                    torch.cuda.current_stream())
-    e = ell.cpu().numpy()
     t = dt_phys * np.arange(1, steps + 1)
-    out = {"workload": f"periodic CH, L=2pi, N=256, gamma=0.01, dt=0.1dx, T=100 ({steps} steps), "
-                       f"M=2^16, C0~U[-0.1,0.1], FP64",
-           "s_total": ms / 1e3, "ms_per_step": ms / steps, "finite": bool(np.all(np.isfinite(e))),
-           "ell_at_t": {str(tt): float(e[int(round(tt / dt_phys)) - 1]) for tt in (1, 10, 50, 100)}}
-    for lo in (1.0, 10.0):
-        sel = t >= lo
-        out[f"r_log_fit_t{int(lo)}_100"] = float(np.corrcoef(np.log(t[sel]), e[sel])[0, 1])
-    out["paper_r_2pi"] = 0.9989
+    out = {"workload": f"periodic CH, dx=2pi/256, gamma=0.01, dt=0.1dx, T=100 ({steps} steps), "
+                       f"M={M}, C0~U[-0.1,0.1], FP64 (fused steps, ell reduced every step)"}
+    for name, N, paper_r in (("L_2pi", 256, 0.9989), ("L_4pi", 512, 0.9996)):
+        st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, gamma_grid, dt_grid)
+        C = synth.torch_uniform(4, N, M, -0.1, 0.1, torch.float64, "cuda")
+        ell = torch.zeros(steps, dtype=torch.float64, device="cuda")
+        work = torch.empty(M + 256, dtype=torch.float64, device="cuda")
+        ms = _events_ms(lambda: sb.sb_stepper_run_coarsening(st, C, steps, ell, work), 1,
+                        torch.cuda.current_stream())
+        e = ell.cpu().numpy()
+        r = {"N": N, "s_total": ms / 1e3, "ms_per_step": ms / steps,
+             "finite": bool(np.all(np.isfinite(e))),
+             "ell_at_t": {str(tt): float(e[int(round(tt / dt_phys)) - 1]) for tt in (1, 10, 50, 100)}}
+        for lo in (1.0, 10.0):
+            sel = t >= lo
+            r[f"r_log_fit_t{int(lo)}_100"] = float(np.corrcoef(np.log(t[sel]), e[sel])[0, 1])
+        r["paper_r"] = paper_r
+        out[name] = r
+        del C, ell, work
+        torch.cuda.empty_cache()
+    return out
+
+
+def extra_convergence(sb, torch, stream):
+    """The paper's convergence study of the periodic CH scheme (section 5.2, Table 3):
+    gamma = 0.01, L = 2 pi, dt = 0.1 dx, C(x, 0) = 1e-6 cos(5 x), T = 20, one
+    simulation per grid, N = 64 .. OPTIONS["table3_max_n"].  E_N = mean over the N/2
+    shared points of |C^(N/2) - C^(N)|, with the paper's printed E_N beside it."""
+    import math
+    import numpy as np
+    import synth
+    paper = {128: (0.0310, 3.7932), 256: (0.0022, 2.0376), 512: (5.45e-4, 2.0089),
+             1024: (1.35e-4, 2.0022), 2048: (3.38e-5, 2.0005), 4096: (8.45e-6, 0.8947),
+             8192: (4.54e-6, None)}
+    Ns = [n for n in synth.WORKLOADS["ch_convergence"]["N"] if n <= OPTIONS["table3_max_n"]]
+    runs, secs = {}, {}
+    for N in Ns:
+        gamma, dt, steps, _, C0 = synth.ch_convergence_case(N)
+        st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, gamma, dt)
+        d = torch.from_numpy(np.ascontiguousarray(C0)).cuda()
+        secs[N] = _events_ms(lambda: sb.sb_stepper_run(st, d, steps), 1, torch.cuda.current_stream()) / 1e3
+        runs[N] = d.cpu().numpy()[:, 0]
+    rows = {}
+    for N in Ns[1:]:
+        e = float(np.mean(np.abs(runs[N // 2] - runs[N][::2])))
+        rows[N] = {"E_N": e, "paper_E_N": paper[N][0], "s_run": secs[N]}
+    for N in Ns[1:-1]:
+        rows[N]["order"] = math.log2(rows[N]["E_N"] / rows[2 * N]["E_N"])
+        rows[N]["paper_order"] = paper[N][1]
+    return {"workload": "periodic CH, L=2pi, gamma=0.01, dt=0.1dx, C0=1e-6 cos(5x), T=20, M=1, FP64",
+            "rows": {str(k): v for k, v in rows.items()}}
+
+
+def extra_forced(sb, torch, stream):
+    """The travelling-wave forced CH scheme of section 6.1 (WENO advection and forcing
+    fused into the periodic CH step): (a) the paper's forced convergence study
+    (Table 4) on N = 128 .. OPTIONS["table3_max_n"], one simulation per grid, with the
+    printed E_N beside ours; (b) the flow-pattern batch of section 6.3: N = 512 on
+    L = 2 pi, 768 x 768 = 589 824 simulations over f0 in [0, 2] and <C> in [0, 1.5],
+    k = 1, v = 0.5, gamma = 0.01, dt = 0.1 dx, C0 = <C> + U[-0.1, 0.1]: the time per
+    step over 2 graphs of 64 steps, and that rate applied to the paper's T = 50."""
+    import math
+    import numpy as np
+    import synth
+    out = {}
+    w = synth.WORKLOADS["forced_ch_convergence"]
+    paper = {256: (0.0013, 2.8363), 512: (1.8e-4, 1.9869), 1024: (4.54e-5, 2.0086), 2048: (1.13e-5, 1.9673),
+             4096: (2.88e-5, None)}
+    Ns = [n for n in w["N"] if n <= OPTIONS["table3_max_n"]]
+    runs = {}
+    for N in Ns:
+        gamma, dt, steps, dtp, C0 = synth.forced_ch_convergence_case(N)
+        dx = 2.0 * math.pi / N
+        st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, gamma, dt)
+        sb.sb_stepper_set_forcing(st, dtp * w["v"] / dx, dtp * w["k"] * np.cos(w["k"] * dx * np.arange(N)))
+        d = torch.from_numpy(np.ascontiguousarray(C0)).cuda()
+        a = torch.full((1,), w["f0"], dtype=torch.float64, device="cuda")
+        sb.sb_stepper_run_forced(st, d, a, steps)
+        runs[N] = d.cpu().numpy()[:, 0]
+    rows = {}
+    for N in Ns[1:]:
+        rows[N] = {"E_N": float(np.mean(np.abs(runs[N // 2] - runs[N][::2]))), "paper_E_N": paper[N][0]}
+    for N in Ns[1:-1]:
+        rows[N]["order"] = math.log2(rows[N]["E_N"] / rows[2 * N]["E_N"])
+        rows[N]["paper_order"] = paper[N][1]
+    out["table4"] = {"workload": "forced periodic CH, L=2pi, gamma=0.01, k=1, v=0.5, f0=1, dt=0.1dx, "
+                                 "C0=1e-6 cos(5x), T=20, M=1, FP64",
+                     "rows": {str(k): v for k, v in rows.items()}}
+    m = synth.WORKLOADS["forced_ch_map"]
+    N, side = m["N"], m["side"]
+    M = side * side
+    dx = 2.0 * math.pi / N
+    dtp = m["dt_over_dx"] * dx
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, m["gamma"] / dx ** 2, dtp / dx ** 2)
+    sb.sb_stepper_set_forcing(st, dtp * m["v"] / dx, dtp * m["k"] * np.cos(m["k"] * dx * np.arange(N)))
+    f0 = torch.linspace(m["f0"][0], m["f0"][1], side, dtype=torch.float64, device="cuda")
+    mean = torch.linspace(m["mean"][0], m["mean"][1], side, dtype=torch.float64, device="cuda")
+    amp = f0.repeat_interleave(side).contiguous()          # system a*side + b: f0[a], mean[b]
+    C = synth.torch_uniform(m["seed"], N, M, -m["amp"], m["amp"], torch.float64, "cuda")
+    C += mean.repeat(side)[None, :]
+    sb.sb_stepper_run_forced(st, C, amp, 64)  # warm-up and graph capture
+    ms = _events_ms(lambda: sb.sb_stepper_run_forced(st, C, amp, 128), 1, torch.cuda.current_stream()) / 128
+    steps_T = int(math.ceil(m["T"] / dtp))
+    out["flow_pattern_batch"] = {
+        "workload": f"forced periodic CH, N={N}, M={M} (768 x 768 grid of f0 in [0,2], <C> in [0,1.5]), "
+                    f"k=1, v=0.5, gamma=0.01, dt=0.1dx, FP64, fused + graph",
+        "ms_per_step": ms, "elements_per_s": N * M / (ms / 1e3),
+        "projected_s_for_T50": ms * steps_T / 1e3, "steps_T50": steps_T,
+        "finite": bool(torch.isfinite(C).all().item())}
+    del C, amp
+    return out
+
+
+def _load_cusparse():
+    import ctypes
+    import glob
+    import torch
+    names = ["libcusparse.so.12", "libcusparse.so"]
+    base = os.path.dirname(os.path.dirname(torch.__file__))
+    names += sorted(glob.glob(os.path.join(base, "nvidia", "*", "lib", "libcusparse.so*")))
+    names += sorted(glob.glob("/usr/local/cuda*/lib*/libcusparse.so*"))
+    for n in names:
+        try:
+            return ctypes.CDLL(n), n
+        except OSError:
+            continue
+    return None, "libcusparse not found"
+
+
+def extra_cusparse_context(sb, torch, stream):
+    """Same-box context, not a target: cuSPARSE's interleaved batched solvers, which
+    need a full copy of the matrix per system (the design the paper's constant-matrix
+    kernels replace, section 1): gtsvInterleavedBatch (algorithm 0, no pivoting) on
+    the tridiagonal Table 1 shape (N = 1024, M = 2^16, FP64) and gpsvInterleavedBatch
+    on the pentadiagonal headline workload (N = 1024, M = 2^16, FP64), each timed per
+    solve with CUDA events (the per-system matrix copies are restored before every
+    call, outside the timed region), beside this library's shared-matrix solve of the
+    same systems."""
+    import ctypes
+    import numpy as np
+    import synth
+    lib, where = _load_cusparse()
+    if lib is None:
+        return {"unavailable": where}
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    h = vp()
+    if lib.cusparseCreate(ctypes.byref(h)) != 0:
+        return {"unavailable": "cusparseCreate failed"}
+    cur = torch.cuda.current_stream()
+    lib.cusparseSetStream(h, vp(cur.cuda_stream))
+    out = {"library": os.path.basename(where)}
+    N, M = 1024, 1 << 16
+
+    def timed(fn, restore, reps=10):
+        ts = []
+        for _ in range(reps + 2):
+            restore()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            fn()
+            b.record(cur)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts[2:]))
+
+    for kind in ("tri", "penta"):
+        if kind == "tri":
+            diags = sb.sb_build_matrix("diffusion", N, 0.5)
+            fac = sb.sb_factor_shared_tri(*diags)
+        else:
+            diags = sb.sb_build_matrix("hinged", N, 0.25)
+            fac = sb.sb_factor_shared_penta(*diags)
+        rhs = synth.torch_normal(SEED, N, M, torch.float64, "cuda")
+        full = [torch.from_numpy(np.ascontiguousarray(d)).cuda()[:, None].expand(N, M).contiguous() for d in diags]
+        work = [t.clone() for t in full]
+        xs = rhs.clone()
+        ptr = lambda t: vp(t.data_ptr())
+
+        def restore():
+            for w, f in zip(work, full):
+                w.copy_(f)
+            xs.copy_(rhs)
+        size = ctypes.c_size_t()
+        if kind == "tri":
+            st = lib.cusparseDgtsvInterleavedBatch_bufferSizeExt(h, i32(0), i32(N), ptr(work[0]), ptr(work[1]),
+                                                                 ptr(work[2]), ptr(xs), i32(M), ctypes.byref(size))
+        else:
+            st = lib.cusparseDgpsvInterleavedBatch_bufferSizeExt(h, i32(0), i32(N), ptr(work[0]), ptr(work[1]),
+                                                                 ptr(work[2]), ptr(work[3]), ptr(work[4]), ptr(xs),
+                                                                 i32(M), ctypes.byref(size))
+        if st != 0:
+            out[kind] = {"unavailable": f"bufferSizeExt status {st}"}
+            continue
+        buf = torch.empty(max(1, size.value), dtype=torch.uint8, device="cuda")
+        if kind == "tri":
+            call = lambda: lib.cusparseDgtsvInterleavedBatch(h, i32(0), i32(N), ptr(work[0]), ptr(work[1]),
+                                                             ptr(work[2]), ptr(xs), i32(M), ptr(buf))
+        else:
+            call = lambda: lib.cusparseDgpsvInterleavedBatch(h, i32(0), i32(N), ptr(work[0]), ptr(work[1]),
+                                                             ptr(work[2]), ptr(work[3]), ptr(work[4]), ptr(xs),
+                                                             i32(M), ptr(buf))
+        ms_lib = timed(call, restore)
+        restore()
+        call()
+        x = torch.empty_like(rhs)
+        sb.sb_solve_batched(fac, rhs, x)
+        torch.cuda.synchronize()
+        agree = float(((xs - x).norm(dim=0) / x.norm(dim=0)).max().item())
+        ms_ours = timed(lambda: sb.sb_solve_batched(fac, rhs, x), lambda: None)
+        out[kind] = {"workload": f"{'tridiagonal diffusion r=0.5' if kind == 'tri' else 'pentadiagonal hinged r=0.25'}, "
+                                 f"N={N}, M=2^16, FP64",
+                     "cusparse_routine": "Dgtsv" if kind == "tri" else "Dgpsv",
+                     "cusparse_ms_per_solve": ms_lib, "ours_ms_per_solve": ms_ours,
+                     "speedup": ms_lib / ms_ours, "max_rel_diff_per_system": agree,
+                     "cusparse_matrix_bytes": sum(t.numel() * 8 for t in full)}
+        del full, work, xs, buf, x, rhs
+        torch.cuda.empty_cache()
+    lib.cusparseDestroy(h)
     return out
 
 
@@ -541,7 +749,11 @@ def run_ours(args):
     if not args.no_extras:
         for name, fn in (("tri_latency", extra_tri_latency), ("multigroup_refine", extra_multigroup),
                          ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout),
-                         ("paper_table1_periodic_cn", extra_periodic_cn), ("coarsening", extra_coarsening)):
+                         ("paper_table1_periodic_cn", extra_periodic_cn), ("coarsening", extra_coarsening),
+                         ("paper_table3_convergence", extra_convergence), ("forced_ch", extra_forced),
+                         ("cusparse_context", extra_cusparse_context)):
+            if OPTIONS["extras"] and name not in OPTIONS["extras"]:
+                continue
             try:
                 extras[name] = fn(sb, torch, stream)
             except Exception as exc:  # report, do not hide, a failing extra
@@ -623,7 +835,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arith", choices=["native", "df32"], default="native")
     ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
+    ap.add_argument("--extras", default="", help="comma-separated names of the extras to run (default: all)")
+    ap.add_argument("--coarsening-systems", type=int, default=1 << 16,
+                    help="simulations per domain in the coarsening extra (the paper: 1048576)")
+    ap.add_argument("--table3-max-n", type=int, default=1024,
+                    help="largest grid of the convergence extra (the paper's table: 8192)")
     args = ap.parse_args()
+    OPTIONS.update(extras=[e for e in args.extras.split(",") if e], coarsening_systems=args.coarsening_systems,
+                   table3_max_n=args.table3_max_n)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

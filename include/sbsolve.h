@@ -429,6 +429,32 @@ int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arit
                    int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream);
 
 /*
+ * sb_stepper_set_forcing -- turn a periodic Cahn-Hilliard stepper into the
+ * travelling-wave forced scheme of section 6.1 (the forced equation written in the
+ * frame of the wave, eta = x - v t), in grid units:
+ *   (I + sigma D4_P) C^{n+1} = C^n + alpha D2_P (C^3 - C)^n + adv W(C^n) + amp_m g_i
+ * W is the fifth-order Hamilton-Jacobi WENO derivative (the scheme the paper takes
+ * from Osher and Fedkiw's book, i.e. Jiang and Peng's), biased toward lower rows
+ * (rows i-3..i+2) for adv >= 0 and toward higher rows for adv < 0;
+ * adv = dt v / dx; g (host, N doubles, copied) is the forcing profile, for the paper
+ * g_i = dt k cos(k eta_i); amp_m (per system, given to sb_stepper_run_forced) is the
+ * forcing amplitude f_0 of simulation m.  May be called again to change adv or g.
+ * Native FP64 only.  SB_ERR_UNSUPPORTED for other steppers; SB_ERR_INVALID_ARG for
+ * NULL or non-finite input.  Synchronises the device.
+ */
+int sb_stepper_set_forcing(sb_stepper* st, double adv, const double* g);
+
+/*
+ * sb_stepper_run_forced -- nsteps forced steps of `state` in place (one fused kernel
+ * per step: the right-hand side, WENO term and forcing built inside the forward
+ * sweep; graph-captured in SB_RUN_GRAPH mode).  amp: device array of M doubles.
+ * A forced stepper runs only through this call (sb_stepper_run, the coarsening run
+ * and the rollouts reject it).  Other arguments as for sb_stepper_run.
+ */
+int sb_stepper_run_forced(sb_stepper* st, double* state, const double* amp, int64_t M, int64_t ld,
+                          int64_t nsteps, int mode, void* stream);
+
+/*
  * sb_stepper_run_coarsening -- nsteps fused Cahn-Hilliard steps (as
  * sb_stepper_run with SB_RUN_DIRECT) that also record section 5.3's typical domain
  * size after every step: ell[n] = mean over the M systems of 1 / (1 - <C^2>), with

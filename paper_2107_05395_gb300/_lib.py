@@ -104,6 +104,8 @@ SIGNATURES = {
                                       ctypes.c_size_t, _vp]),
     "sb_stepper_run_coarsening": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, _vp, _vp,
                                                  ctypes.c_size_t, _vp]),
+    "sb_stepper_set_forcing": (ctypes.c_int, [_vp, ctypes.c_double, _dp]),
+    "sb_stepper_run_forced": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, ctypes.c_int, _vp]),
     "sb_device_timeouts": (ctypes.c_int, [ctypes.c_int, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
@@ -460,6 +462,24 @@ def sb_stepper_run(st: Stepper, state, nsteps, arith="native", mode="graph", wor
     _check(lib().sb_stepper_run(st.handle, _dev_ptr(state), M, ld, _arith_code(arith), int(nsteps),
                                 RUN_MODES[mode] if isinstance(mode, str) else int(mode), wptr or None,
                                 wbytes, _stream_handle(stream)))
+    return state
+
+
+def sb_stepper_set_forcing(st: Stepper, adv, profile):
+    """Make a periodic Cahn-Hilliard stepper the travelling-wave forced scheme:
+    adv * W(C) + amp_m * profile_i is added to each step's right-hand side
+    (adv = dt v / dx in grid units; profile: N host values, copied)."""
+    g = _host_f64(profile, st.N)
+    _check(lib().sb_stepper_set_forcing(st.handle, float(adv), g.ctypes.data_as(_dp)))
+
+
+def sb_stepper_run_forced(st: Stepper, state, amp, nsteps, mode="graph", M=None, ld=None, stream=None):
+    """Advance `state` by nsteps forced steps in place; `amp` is a device FP64 tensor of
+    M per-system forcing amplitudes."""
+    M, ld = _batch_shape(state, st.N, M, ld)
+    _check(lib().sb_stepper_run_forced(st.handle, _dev_ptr(state), _dev_ptr(amp), M, ld, int(nsteps),
+                                       RUN_MODES[mode] if isinstance(mode, str) else int(mode),
+                                       _stream_handle(stream)))
     return state
 
 

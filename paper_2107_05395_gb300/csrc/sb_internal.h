@@ -116,8 +116,13 @@ struct sb_stepper {
   double* r64 = nullptr;  // device rhs coefficient rows, FP64
   float* rdf = nullptr;   // same as (hi, lo) pairs
   double* dA64 = nullptr;  // d A / d coef row by row ((2P+1) per row), for the rollout adjoint
+  // travelling-wave forcing (section 6.1): adv * W(C) + amp[m] * g[i] on the right-hand side
+  bool forced = false;
+  double adv = 0.0;
+  double* g64 = nullptr;  // device forcing profile, N values
   std::mutex mu;
   std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t>, cudaGraphExec_t> forced_graphs;
 };
 
 namespace sb {
@@ -174,5 +179,4 @@ int launch_partitioned(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream);
-
 }  // namespace sb

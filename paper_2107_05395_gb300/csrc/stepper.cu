@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <mutex>
 #include <tuple>
 
@@ -49,35 +50,98 @@ __host__ __device__ constexpr int step_cyc_len(int rank, int N) {
   return rank == 1 ? 2 * N : rank == 2 ? 4 * N + 12 : 0;
 }
 
+// Fifth-order Hamilton-Jacobi WENO derivative (Jiang and Peng's scheme, the one the
+// paper takes for its advection term, section 6.1) at the centre of the window
+// c[0..6] = C_{i-3..i+3}, grid spacing 1.  SIDE = -1: the stencil biased toward
+// lower rows (differences D_{i-3}..D_{i+1}, D_j = C_{j+1} - C_j); SIDE = +1: toward
+// higher rows (D_{i+2}..D_{i-2}).  Three third-order candidates, smoothness
+// indicators S_k, eps = 1e-6 max q^2 + 1e-99 and weights (0.1, 0.6, 0.3)/(S_k+eps)^2
+// normalised.  The weights are formed with the (S_k + eps) scaled by their maximum
+// (each ratio then lies in [~5e-8, 1], so no product under- or overflows) and one
+// division, which equals the normalised form up to rounding.
+template <int SIDE>
+__device__ __forceinline__ double weno5(const double (&c)[7]) {
+  double q1, q2, q3, q4, q5;
+  if constexpr (SIDE < 0) {
+    q1 = c[1] - c[0]; q2 = c[2] - c[1]; q3 = c[3] - c[2]; q4 = c[4] - c[3]; q5 = c[5] - c[4];
+  } else {
+    q1 = c[6] - c[5]; q2 = c[5] - c[4]; q3 = c[4] - c[3]; q4 = c[3] - c[2]; q5 = c[2] - c[1];
+  }
+  const double p1 = q1 * (1.0 / 3.0) - q2 * (7.0 / 6.0) + q3 * (11.0 / 6.0);
+  const double p2 = -q2 * (1.0 / 6.0) + q3 * (5.0 / 6.0) + q4 * (1.0 / 3.0);
+  const double p3 = q3 * (1.0 / 3.0) + q4 * (5.0 / 6.0) - q5 * (1.0 / 6.0);
+  const double d1 = q1 - 2.0 * q2 + q3, e1 = q1 - 4.0 * q2 + 3.0 * q3;
+  const double d2 = q2 - 2.0 * q3 + q4, e2 = q2 - q4;
+  const double d3 = q3 - 2.0 * q4 + q5, e3 = 3.0 * q3 - 4.0 * q4 + q5;
+  const double s1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
+  const double s2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
+  const double s3 = (13.0 / 12.0) * d3 * d3 + 0.25 * e3 * e3;
+  const double qm = fmax(fmax(fmax(q1 * q1, q2 * q2), fmax(q3 * q3, q4 * q4)), q5 * q5);
+  const double eps = 1e-6 * qm + 1e-99;
+  const double t1 = s1 + eps, t2 = s2 + eps, t3 = s3 + eps;
+  const double inv = 1.0 / fmax(fmax(t1, t2), t3);
+  const double r1 = t1 * inv, r2 = t2 * inv, r3 = t3 * inv;
+  const double r12 = r1 * r2, r13 = r1 * r3, r23 = r2 * r3;
+  const double w1 = 0.1 * (r23 * r23), w2 = 0.6 * (r13 * r13), w3 = 0.3 * (r12 * r12);
+  return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
+}
+
 // STATS: each system's new state also gives ell_m = 1 / (1 - <C^2>), <C^2> the mean
 // of C_i^2 over its N rows (section 5.3's coarsening length), written to ellm[m].
-template <class A, int P, int NB, bool HAS_E, int R, int CYC, bool STATS = false>
+// GC: the coefficient rows do not fit in shared memory (large N) and are read from
+// their device copies directly (warp-uniform loads, served by L1/L2).
+// ADV (periodic Cahn-Hilliard, native FP64 only): the travelling-wave forced scheme
+// of section 6.1 adds adv * W(C^n) + amp[m] * g[i] to the right-hand side, with W
+// the fifth-order Hamilton-Jacobi WENO derivative biased toward lower rows (ADV = -1,
+// rows i-3..i+2) or higher rows (ADV = +1, rows i-2..i+3); the state window then
+// spans rows i-3..i+3 instead of i-2..i+2.
+template <class A, int P, int NB, bool HAS_E, int R, int CYC, bool STATS = false, bool GC = false,
+          int ADV = 0>
 __global__ void __launch_bounds__(512)
 fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* __restrict__ rcoef,
                   int N, int64_t M, int64_t ld, const double* src, double* state, int64_t ntiles,
                   const typename A::C* __restrict__ cyc, typename A::C alpha, typename A::C beta,
-                  double* __restrict__ ellm = nullptr) {
+                  double* __restrict__ ellm = nullptr, const double* __restrict__ gprof = nullptr,
+                  const double* __restrict__ amp = nullptr, double adv = 0.0) {
   using V = typename A::V;
   using C = typename A::C;
   using S = typename A::S;
   constexpr int W = P + 1;
   constexpr int NE = HAS_E ? 3 : 0;
   constexpr int RW = NB + NE;  // rhs coefficients per row
+  constexpr int LA = ADV != 0 ? 3 : 2;  // rows of look-ahead (and look-behind) in the window
+  constexpr int LW = 2 * LA + 1;
+  static_assert(ADV == 0 || (std::is_same_v<V, double> && CYC == 2 && HAS_E),
+                "the forced scheme is periodic Cahn-Hilliard in native FP64");
+  static_assert(R >= LA, "the look-ahead must fit in one prefetch batch");
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* cs = reinterpret_cast<C*>(smem_raw);
-  {
+  const C* fw;
+  const C* rc;
+  const C* cy;
+  const double* gp;
+  if constexpr (GC) {
+    fw = coef;
+    rc = rcoef;
+    cy = cyc;
+    gp = gprof;
+  } else {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* cs = reinterpret_cast<C*>(smem_raw);
     const int n = 2 * W * N;
     for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = coef[k];
     for (int k = threadIdx.x; k < RW * N; k += blockDim.x) cs[n + k] = rcoef[k];
     if constexpr (CYC != 0)
       for (int k = threadIdx.x; k < step_cyc_len(CYC, N); k += blockDim.x) cs[n + RW * N + k] = cyc[k];
+    double* gs = reinterpret_cast<double*>(cs + n + RW * N + step_cyc_len(CYC, N));
+    if constexpr (ADV != 0)
+      for (int k = threadIdx.x; k < N; k += blockDim.x) gs[k] = gprof[k];
+    __syncthreads();
+    fw = cs;
+    rc = cs + n;
+    cy = rc + RW * N;
+    gp = gs;
   }
-  __syncthreads();
-  const C* fw = cs;
-  const C* bw = cs + W * N;
-  const C* rc = cs + 2 * W * N;
-  const C* cy = rc + RW * N;
+  const C* bw = fw + W * N;
 
   const int lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
@@ -88,10 +152,10 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     double* y = state + m;     // intermediates and the new state
     const double* c = src + m;  // the old state (may be the same array as y)
 
-    // window: cw[k] = C_{i-2+k}, pw[k] = phi(C_{i-1+k}) for the row i being built
-    V cw[5], pw[3];
+    // window: cw[k] = C_{i-LA+k}, pw[k] = phi(C_{i-1+k}) for the row i being built
+    V cw[LW], pw[3];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) cw[k] = A::zero();
+    for (int k = 0; k < LW; ++k) cw[k] = A::zero();
 #pragma unroll
     for (int k = 0; k < 3; ++k) pw[k] = A::zero();
     double va[R], vb[R];
@@ -103,30 +167,36 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     // push raw row k (value v, already 0 when k >= N) into the windows
     auto push = [&](double v) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cw[k] = cw[k + 1];
-      cw[4] = StConv<A, double>::in(v);
+      for (int k = 0; k < LW - 1; ++k) cw[k] = cw[k + 1];
+      cw[LW - 1] = StConv<A, double>::in(v);
       if constexpr (HAS_E) {
         pw[0] = pw[1];
         pw[1] = pw[2];
-        pw[2] = A::cubic(cw[3]);  // phi(C_{i+1}) once C_{i+1} entered the window
+        pw[2] = A::cubic(cw[LA + 1]);  // phi(C_{i+1}) once C_{i+1} entered the window
       }
     };
+    double fm = 0.0;  // this system's forcing amplitude
+    if constexpr (ADV != 0) fm = amp[m];
     V u1 = A::zero(), u2 = A::zero(), dot = A::zero(), dot1 = A::zero();
     auto build_and_sweep = [&](int i) {
       V r;
       if constexpr (NB > 0) {
         const C* b = rc + RW * i;
-        r = A::mulc(b[0], cw[2 - NB / 2]);
+        r = A::mulc(b[0], cw[LA - NB / 2]);
 #pragma unroll
-        for (int k = 1; k < NB; ++k) r = A::fmac(b[k], cw[2 - NB / 2 + k], r);
+        for (int k = 1; k < NB; ++k) r = A::fmac(b[k], cw[LA - NB / 2 + k], r);
       } else {
-        r = cw[2];
+        r = cw[LA];
       }
       if constexpr (HAS_E) {
         const C* e = rc + RW * i + NB;
         r = A::fmac(e[0], pw[0], r);
         r = A::fmac(e[1], pw[1], r);
         r = A::fmac(e[2], pw[2], r);
+      }
+      if constexpr (ADV != 0) {
+        r = fma(adv, weno5<ADV>(cw), r);
+        r = fma(fm, gp[i], r);
       }
       const V u = A::template step<P, false>(fw + W * i, r, u1, u2);
       if constexpr (CYC == 1) dot = A::fmac(cy[2 * i], r, dot);
@@ -143,27 +213,29 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
     // forward sweep overwrites anything)
     load_rows(va, 0);
     load_rows(vb, R);
-    double c0 = 0.0, c1 = 0.0;
+    double cpre[LA];  // rows 0..LA-1, which wrap in as rows N..N+LA-1
+#pragma unroll
+    for (int k = 0; k < LA; ++k) cpre[k] = 0.0;
     if constexpr (CYC != 0) {
-      c0 = va[0];
-      c1 = va[1];  // N >= 3 (rank 1) or 5 (rank 2), and R >= 2
-      // three pushes (rows 0, 1, 2) precede the build of row 0 and each shifts the
-      // window left by one, so the last two slots end up holding rows -2 and -1
-      cw[3] = StConv<A, double>::in(c[(int64_t)(N - 2) * ld]);
-      cw[4] = StConv<A, double>::in(c[(int64_t)(N - 1) * ld]);
+#pragma unroll
+      for (int k = 0; k < LA; ++k) cpre[k] = va[k];  // N >= 3 (rank 1) or 5 (rank 2), R >= LA
+      // LA + 1 pushes (rows 0..LA) precede the build of row 0 and each shifts the
+      // window left by one, so the last LA slots end up holding rows -LA..-1
+#pragma unroll
+      for (int k = 0; k < LA; ++k)
+        cw[LW - LA + k] = StConv<A, double>::in(c[(int64_t)(N - LA + k) * ld]);
     }
-    push(N > 0 ? va[0] : 0.0);
-    push(N > 1 ? va[1] : 0.0);
-    // row i needs raw row i + 2: from the current buffer or the next one
+#pragma unroll
+    for (int k = 0; k < LA; ++k) push(N > k ? va[k] : 0.0);
+    // row i needs raw row i + LA: from the current buffer or the next one
+    auto ahead = [&](int i, double v) { return (i + LA < N) ? v : (CYC != 0 ? cpre[i + LA - N] : 0.0); };
     for (int i0 = 0; i0 < N; i0 += 2 * R) {
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int i = i0 + j;
         if (i < N) {
-          const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? va[k] : vb[k - R])
-                                       : (CYC != 0 ? (i + 2 == N ? c0 : c1) : 0.0);
-          push(v);
+          const int k = j + LA;
+          push(ahead(i, k < R ? va[k] : vb[k - R]));
           build_and_sweep(i);
         }
       }
@@ -172,10 +244,8 @@ fused_step_kernel(const typename A::C* __restrict__ coef, const typename A::C* _
       for (int j = 0; j < R; ++j) {
         const int i = i0 + R + j;
         if (i < N) {
-          const int k = j + 2;
-          const double v = (i + 2 < N) ? (k < R ? vb[k] : va[k - R])
-                                       : (CYC != 0 ? (i + 2 == N ? c0 : c1) : 0.0);
-          push(v);
+          const int k = j + LA;
+          push(ahead(i, k < R ? vb[k] : va[k - R]));
           build_and_sweep(i);
         }
       }
@@ -330,18 +400,28 @@ struct StepCyc<DFArith> {
   }
 };
 
-template <class A, int P, int NB, bool HAS_E, int CYC, bool STATS = false>
+template <class A, int P, int NB, bool HAS_E, int CYC, bool STATS = false, int ADV = 0>
 int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename A::C* rc,
                  const double* src, double* state, int64_t M, int64_t ld, cudaStream_t stream,
-                 double* ellm = nullptr) {
+                 double* ellm = nullptr, const double* amp = nullptr) {
   const sb_factor* f = st->fac;
   const int N = (int)f->N;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
-  const size_t smem =
-      ((size_t)2 * (P + 1) * N + (size_t)RW * N + (size_t)step_cyc_len(CYC, N)) * sizeof(typename A::C);
-  if (smem > 227 * 1024)
-    return fail(SB_ERR_UNSUPPORTED, "N=%d too large for the fused step's shared memory", N);
-  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC, STATS>;
+  size_t smem =
+      ((size_t)2 * (P + 1) * N + (size_t)RW * N + (size_t)step_cyc_len(CYC, N)) * sizeof(typename A::C) +
+      (ADV != 0 ? (size_t)N * sizeof(double) : 0);
+  auto k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC, STATS, false, ADV>;
+  if (smem > (size_t)kMaxDynSmem) {
+    // FP64 coefficients of a large N are read from device memory
+    if constexpr (std::is_same_v<A, NativeArith<double>>) {
+      k = fused_step_kernel<A, P, NB, HAS_E, kStepRows, CYC, STATS, true, ADV>;
+      smem = 0;
+    } else {
+      return fail(SB_ERR_UNSUPPORTED,
+                  "N=%d too large for the fused step's shared memory (only FP64 steps read the "
+                  "coefficients from device memory)", N);
+    }
+  }
   const int threads = 256;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, int> occ;
@@ -364,8 +444,20 @@ int launch_fused(const sb_stepper* st, const typename A::C* coef, const typename
   const typename A::C* cy = CYC ? StepCyc<A>::rows(f) : nullptr;  // primal rows (op 0)
   k<<<(unsigned)grid, threads, smem, stream>>>(coef, rc, N, M, ld, src, state, ntiles, cy,
                                               StepCyc<A>::coef(CYC ? f->cyc_alpha[0] : 0.0),
-                                              StepCyc<A>::coef(CYC ? f->cyc_beta[0] : 0.0), ellm);
+                                              StepCyc<A>::coef(CYC ? f->cyc_beta[0] : 0.0), ellm,
+                                              ADV != 0 ? st->g64 : nullptr, amp, st->adv);
   return cuda_check(cudaGetLastError(), "fused step launch");
+}
+
+// One forced step (periodic Cahn-Hilliard with the travelling-wave terms), in place.
+int one_step_forced(const sb_stepper* st, double* state, const double* amp, int64_t M, int64_t ld,
+                    cudaStream_t stream) {
+  using A = NativeArith<double>;
+  return st->adv >= 0.0
+             ? launch_fused<A, 2, 0, true, 2, false, -1>(st, st->fac->coef64, st->r64, state, state, M,
+                                                         ld, stream, nullptr, amp)
+             : launch_fused<A, 2, 0, true, 2, false, +1>(st, st->fac->coef64, st->r64, state, state, M,
+                                                         ld, stream, nullptr, amp);
 }
 
 template <class A, int NB, bool HAS_E, bool CYC>
@@ -564,6 +656,8 @@ void sb_stepper_destroy(sb_stepper* st) {
   if (st->fac) {
     DeviceGuard g(st->fac->device);
     for (auto& kv : st->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : st->forced_graphs) cudaGraphExecDestroy(kv.second);
+    if (st->g64) cudaFree(st->g64);
     if (st->r64) cudaFree(st->r64);
     if (st->rdf) cudaFree(st->rdf);
     sb_factor_destroy(st->fac);
@@ -573,13 +667,95 @@ void sb_stepper_destroy(sb_stepper* st) {
 
 const sb_factor* sb_stepper_factor(const sb_stepper* st) { return st ? st->fac : nullptr; }
 
+int sb_stepper_set_forcing(sb_stepper* st, double adv, const double* profile) {
+  clear_error();
+  if (!st || !profile) return fail(SB_ERR_INVALID_ARG, "NULL argument");
+  if (st->kind != SB_STEP_CAHN_HILLIARD || st->bc != SB_BC_PERIODIC)
+    return fail(SB_ERR_UNSUPPORTED, "the travelling-wave forcing needs a periodic Cahn-Hilliard stepper");
+  if (!std::isfinite(adv)) return fail(SB_ERR_INVALID_ARG, "non-finite advection coefficient");
+  const int64_t N = st->N;
+  for (int64_t i = 0; i < N; ++i)
+    if (!std::isfinite(profile[i])) return fail(SB_ERR_INVALID_ARG, "non-finite forcing at row %lld", (long long)i);
+  DeviceGuard g(st->fac->device);
+  SB_TRY(g.rc);
+  std::lock_guard<std::mutex> lk(st->mu);
+  if (!st->g64) SB_CUDA(cudaMalloc(&st->g64, (size_t)N * sizeof(double)));
+  // captured graphs read the old values through the same pointer, so they stay valid;
+  // the advection coefficient is a launch argument, so they are rebuilt
+  SB_CUDA(cudaDeviceSynchronize());
+  SB_CUDA(cudaMemcpy(st->g64, profile, (size_t)N * sizeof(double), cudaMemcpyHostToDevice));
+  for (auto& kv : st->forced_graphs) cudaGraphExecDestroy(kv.second);
+  st->forced_graphs.clear();
+  st->adv = adv;
+  st->forced = true;
+  return SB_OK;
+}
+
+int sb_stepper_run_forced(sb_stepper* st, double* state, const double* amp, int64_t M, int64_t ld,
+                          int64_t nsteps, int mode, void* stream) {
+  clear_error();
+  if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
+  if (!st->forced) return fail(SB_ERR_INVALID_ARG, "the stepper has no forcing (sb_stepper_set_forcing)");
+  if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (mode != SB_RUN_GRAPH && mode != SB_RUN_DIRECT)
+    return fail(SB_ERR_INVALID_ARG, "forced runs support SB_RUN_GRAPH and SB_RUN_DIRECT");
+  const sb_factor* f = st->fac;
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  if (M < 0 || ld < M || ld < 1) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  if (M == 0 || nsteps == 0) return SB_OK;
+  const size_t bytes = (size_t)((f->N - 1) * ld + M) * sizeof(double);
+  SB_TRY(check_device_range(state, bytes, sizeof(double), f->device, "state"));
+  SB_TRY(check_device_range(amp, (size_t)M * sizeof(double), sizeof(double), f->device, "amp"));
+  SB_TRY(check_alias(state, bytes, amp, (size_t)M * sizeof(double), "state", "amp"));
+  cudaStream_t s = (cudaStream_t)stream;
+  bool capturing = false;
+  if (mode == SB_RUN_GRAPH && s != nullptr) {
+    cudaStreamCaptureStatus cs;
+    SB_CUDA(cudaStreamIsCapturing(s, &cs));
+    capturing = (cs != cudaStreamCaptureStatusNone);
+  }
+  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
+    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(one_step_forced(st, state, amp, M, ld, s));
+    return SB_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(st->mu);
+    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(amp), M, ld);
+    auto it = st->forced_graphs.find(key);
+    if (it != st->forced_graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t graph = nullptr;
+      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int rc = SB_OK;
+      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = one_step_forced(st, state, amp, M, ld, s);
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc != SB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      SB_CUDA(e);
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SB_CUDA(e);
+      st->forced_graphs[key] = exec;
+    }
+  }
+  int64_t n = 0;
+  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
+  for (; n < nsteps; ++n) SB_TRY(one_step_forced(st, state, amp, M, ld, s));
+  return SB_OK;
+}
+
 int sb_stepper_run_coarsening(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
                               int64_t nsteps, double* ell, void* work, size_t work_bytes,
                               void* stream) {
   clear_error();
   if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
-  if (st->kind != SB_STEP_CAHN_HILLIARD)
-    return fail(SB_ERR_UNSUPPORTED, "the coarsening statistic needs a Cahn-Hilliard stepper");
+  if (st->kind != SB_STEP_CAHN_HILLIARD || st->forced)
+    return fail(SB_ERR_UNSUPPORTED, "the coarsening statistic needs an unforced Cahn-Hilliard stepper");
   if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
     return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode %d", (int)arith);
@@ -626,6 +802,7 @@ int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arit
                    int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream) {
   clear_error();
   if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
+  if (st->forced) return fail(SB_ERR_INVALID_ARG, "a forced stepper runs through sb_stepper_run_forced");
   if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (arith != SB_ARITH_NATIVE && arith != SB_ARITH_DF32)
     return fail(SB_ERR_INVALID_ARG, "unknown arithmetic mode %d", (int)arith);

@@ -29,25 +29,36 @@ __host__ __device__ constexpr int cyc_len(int rank, int N) { return rank == 1 ? 
 // Single-factor kernel: persistent CTAs stage the coefficients once, then their
 // warps take tiles round-robin over the grid.  CYC: periodic matrices (rank-1
 // tridiagonal of section 3.3, rank-2 cyclic pentadiagonal); the correction data is
-// staged after the coefficients.
+// staged after the coefficients.  GC: the factors do not fit in shared memory
+// (large N), so the sweeps read the single device copy directly (warp-uniform
+// loads, served by L1/L2) instead of a staged one.
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int SPT, int R,
-          int CYC>
+          int CYC, bool GC = false>
 __global__ void __launch_bounds__(512)
 sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld,
              const TI* rhs, TO* x, int64_t ntiles, const typename A::C* __restrict__ cyc,
              typename A::C alpha, typename A::C beta) {
   using C = typename A::C;
   constexpr int W = P + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* cs = reinterpret_cast<C*>(smem_raw);
-  stage(cs, coef, 2 * W * N);
-  if constexpr (CYC) stage(cs + 2 * W * N, cyc, cyc_len(CYC, N));
-  __syncthreads();
+  const C* fw;
+  const C* cy;
+  if constexpr (GC) {
+    fw = coef;
+    cy = cyc;
+  } else {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* cs = reinterpret_cast<C*>(smem_raw);
+    stage(cs, coef, 2 * W * N);
+    if constexpr (CYC) stage(cs + 2 * W * N, cyc, cyc_len(CYC, N));
+    __syncthreads();
+    fw = cs;
+    cy = cs + 2 * W * N;
+  }
   const int nw = blockDim.x >> 5;
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
        tile += (int64_t)gridDim.x * nw)
-    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC>(cs, cs + W * N, N, M, ld, rhs, x, tile,
-                                                         cs + 2 * W * N, alpha, beta);
+    sweep_tile<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC>(fw, fw + W * N, N, M, ld, rhs, x, tile,
+                                                         cy, alpha, beta);
 }
 
 // The periodic correction data of a factor for an arithmetic policy: (w_i, -z_i)
@@ -88,11 +99,21 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
            int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
   using C = typename A::C;
   const int N = (int)f->N;
-  const size_t smem = ((size_t)2 * (P + 1) * N + (size_t)cyc_len(CYC, N)) * sizeof(C);
-  if (smem > 227 * 1024)
-    return fail(SB_ERR_UNSUPPORTED,
-                "N=%d: the shared factors (%zu B) exceed the shared memory of one CTA", N, smem);
+  size_t smem = ((size_t)2 * (P + 1) * N + (size_t)cyc_len(CYC, N)) * sizeof(C);
   auto k = sweep_kernel<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC>;
+  if (smem > (size_t)kMaxDynSmem) {
+    // FP64 factors of a large N are read from device memory; the other policies
+    // keep the staged form only
+    if constexpr (std::is_same_v<A, NativeArith<double>> && std::is_same_v<TI, double> &&
+                  std::is_same_v<TO, double>) {
+      k = sweep_kernel<A, P, F_ONE, B_ONE, TI, TO, SPT, R, CYC, true>;
+      smem = 0;
+    } else {
+      return fail(SB_ERR_UNSUPPORTED,
+                  "N=%d: the shared factors (%zu B) exceed the shared memory of one CTA "
+                  "(only FP64 solves read them from device memory)", N, smem);
+    }
+  }
   const int threads = shape.threads;
   if (threads < 32 || threads > 512 || threads % 32 != 0)
     return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, 512]");

@@ -57,3 +57,34 @@ def test_host_solve_in_place_and_errors(env):
     dev = torch.zeros((N, M), dtype=torch.float64, device="cuda")
     with pytest.raises(sb.SbError):  # device memory where host memory is expected
         sb.sb_solve_batched_host(fac, dev, t, work, chunk_systems=128)
+
+
+@pytest.mark.parametrize("kind", ["penta", "tri_periodic", "penta_periodic"])
+def test_chunking_does_not_change_the_bits(env, kind):
+    """The chunk size only changes which copies overlap which solves: the default
+    chunking and 128-system chunks give the same bits (each system's arithmetic is
+    the same), in place too, for A and A^T, periodic and not."""
+    sb, torch = env
+    N, M, ld = 300, 777, 800
+    if kind == "penta":
+        fac = sb.sb_factor_shared_penta(*synth.random_penta_diagonals(seed=8, N=N))
+    elif kind == "tri_periodic":
+        fac = sb.sb_factor_shared_tri_periodic(*sb.sb_build_matrix("diffusion_periodic", N, 0.6))
+    else:
+        fac = sb.sb_factor_shared_penta_periodic(*sb.sb_build_matrix("ch_periodic", N, 0.4))
+    host = synth.rhs_normal(seed=9, N=N, M=M, ld=ld, pad_value=-1.5)
+    for transpose in (False, True):
+        rhs = torch.from_numpy(host.copy()).pin_memory()
+        outs = []
+        for chunk in (0, 128):
+            x = torch.full_like(rhs, -1.5).pin_memory()
+            work = torch.empty(sb.sb_host_workspace_bytes(fac, M, chunk), dtype=torch.uint8, device="cuda")
+            sb.sb_solve_batched_host(fac, rhs, x, work, transpose=transpose, chunk_systems=chunk, M=M)
+            torch.cuda.synchronize()
+            outs.append(x.numpy().copy())
+        assert np.array_equal(outs[0], outs[1])
+        assert np.all(outs[0][:, M:] == -1.5)
+        work = torch.empty(sb.sb_host_workspace_bytes(fac, M), dtype=torch.uint8, device="cuda")
+        sb.sb_solve_batched_host(fac, rhs, rhs, work, transpose=transpose, M=M)  # in place, direct
+        torch.cuda.synchronize()
+        assert np.array_equal(rhs.numpy()[:, :M], outs[0][:, :M])
