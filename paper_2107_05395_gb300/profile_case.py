@@ -1,6 +1,7 @@
 """Runs a few launches of one solver kernel on a chosen size, for profilers.
 
     python -m paper_2107_05395_gb300.profile_case --kind penta --N 1024 --M 32768 --launches 3
+    python -m paper_2107_05395_gb300.profile_case --kind forced_ch --N 512 --M 65536 --launches 3
 
 Everything goes through the C ABI; inputs are seeded N(0, 1) drawn on the device.
 The default case keeps the inputs above the L2 size (so DRAM counters mean
@@ -17,7 +18,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["tri", "penta"], default="penta")
+    ap.add_argument("--kind", choices=["tri", "penta", "forced_ch"], default="penta")
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--M", type=int, default=32768)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -34,6 +35,22 @@ def main():
     import synth
 
     dt = torch.float64 if args.dtype == "f64" else torch.float32
+    if args.kind == "forced_ch":
+        # one direct (ungraphed) launch per step of the travelling-wave forced CH
+        # scheme with the flow-pattern batch's parameters (k = 1, v = 0.5, gamma = 0.01,
+        # dt = 0.1 dx on L = 2 pi), amplitudes f0 spread over [0, 2]
+        import math
+        N, M = args.N, args.M
+        dx = 2.0 * math.pi / N
+        dtp = 0.1 * dx
+        st = sb.sb_stepper_create("cahn_hilliard", "be", "periodic", N, 0.01 / dx ** 2, dtp / dx ** 2)
+        sb.sb_stepper_set_forcing(st, dtp * 0.5 / dx, [dtp * math.cos(dx * i) for i in range(N)])
+        C = synth.torch_uniform(6, N, M, -0.1, 0.1, torch.float64, "cuda") + 0.5
+        amp = torch.linspace(0.0, 2.0, M, dtype=torch.float64, device="cuda")
+        sb.sb_stepper_run_forced(st, C, amp, args.launches, mode="direct")
+        torch.cuda.synchronize()
+        print(f"ok: {args.launches} forced CH steps N={N} M={M}")
+        return
     if args.kind == "tri":
         fac = sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", args.N, 0.5))
     else:
