@@ -56,9 +56,19 @@ __host__ __device__ constexpr int step_cyc_len(int rank, int N) {
 // lower rows (differences D_{i-3}..D_{i+1}, D_j = C_{j+1} - C_j); SIDE = +1: toward
 // higher rows (D_{i+2}..D_{i-2}).  Three third-order candidates, smoothness
 // indicators S_k, eps = 1e-6 max q^2 + 1e-99 and weights (0.1, 0.6, 0.3)/(S_k+eps)^2
-// normalised.  The weights are formed with the (S_k + eps) scaled by their maximum
-// (each ratio then lies in [~5e-8, 1], so no product under- or overflows) and one
-// division, which equals the normalised form up to rounding.
+// normalised.  GB300's FP64 pipe is the bound here, so what needs no FP64
+// arithmetic runs on the integer pipe: max |q| and max_k (S_k + eps) compare bit
+// patterns (non-negative doubles order like their bits), and the (S_k + eps) are
+// scaled by the power of two that brings their maximum into [1, 2) (built from its
+// exponent field; exact), which keeps every product of the weights in range (each
+// ratio is at least ~1e-8) with one division in all.  The result equals the
+// normalised form up to rounding.
+__device__ __forceinline__ double max_bits(double a, double b) {
+  return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double abs_bits(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
 template <int SIDE>
 __device__ __forceinline__ double weno5(const double (&c)[7]) {
   double q1, q2, q3, q4, q5;
@@ -76,11 +86,15 @@ __device__ __forceinline__ double weno5(const double (&c)[7]) {
   const double s1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
   const double s2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
   const double s3 = (13.0 / 12.0) * d3 * d3 + 0.25 * e3 * e3;
-  const double qm = fmax(fmax(fmax(q1 * q1, q2 * q2), fmax(q3 * q3, q4 * q4)), q5 * q5);
-  const double eps = 1e-6 * qm + 1e-99;
+  const double qa = max_bits(max_bits(max_bits(abs_bits(q1), abs_bits(q2)), max_bits(abs_bits(q3), abs_bits(q4))),
+                             abs_bits(q5));
+  const double eps = fma(1e-6, qa * qa, 1e-99);
   const double t1 = s1 + eps, t2 = s2 + eps, t3 = s3 + eps;
-  const double inv = 1.0 / fmax(fmax(t1, t2), t3);
-  const double r1 = t1 * inv, r2 = t2 * inv, r3 = t3 * inv;
+  // 2^-(e - 1023) for the exponent field e of max t (t >= 1e-99, finite unless the
+  // data is; the clamp only keeps the bit pattern well formed then)
+  const long long ef = (__double_as_longlong(max_bits(max_bits(t1, t2), t3)) >> 52) & 0x7ff;
+  const double scale = __longlong_as_double((2046LL - min(max(ef, 1LL), 2045LL)) << 52);
+  const double r1 = t1 * scale, r2 = t2 * scale, r3 = t3 * scale;
   const double r12 = r1 * r2, r13 = r1 * r3, r23 = r2 * r3;
   const double w1 = 0.1 * (r23 * r23), w2 = 0.6 * (r13 * r13), w3 = 0.3 * (r12 * r12);
   return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
