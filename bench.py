@@ -308,7 +308,8 @@ def extra_multigroup(sb, torch, stream):
 
 def extra_cahn_hilliard(sb, torch, stream):
     """Cahn-Hilliard, N=256, 2^20 simulations: ms per step for the fused + graphed
-    step (FP64 and double-float) and the unfused two-kernel step (FP64)."""
+    step (FP64 and double-float), the unfused two-kernel step, and the FP32 sweeps +
+    2 refinement passes step (with its error against the FP64 step)."""
     import synth
     w = synth.WORKLOADS["cahn_hilliard"]
     N, M = w["N"], w["M"]
@@ -323,6 +324,21 @@ def extra_cahn_hilliard(sb, torch, stream):
                         torch.cuda.current_stream()) / 64
         out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms,
                      "algorithmic_gbs": 16.0 * N * M / (ms * 1e-3) / 1e9}
+    # FP32 sweeps + 2 refinement passes per step (FP64 or double-float residual),
+    # against the fused FP64 step from the same state after 64 steps
+    rwork = torch.empty(sb.sb_stepper_refined_workspace_bytes(st, M), dtype=torch.uint8, device="cuda")
+    C64 = C.clone()
+    sb.sb_stepper_run(st, C64, 64)
+    for name, res in (("fp32_refine2_fp64res", "native"), ("fp32_refine2_df32res", "df32")):
+        Cr = C.clone()
+        sb.sb_stepper_run_refined(st, Cr, 64, rwork, n_refine=2, residual_arith=res)
+        err = float(((Cr - C64).norm(dim=0) / C64.norm(dim=0)).max().item())
+        ms = _events_ms(lambda: sb.sb_stepper_run_refined(st, Cr, 64, rwork, n_refine=2, residual_arith=res), 2,
+                        torch.cuda.current_stream()) / 64
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                     "max_rel_l2_vs_fp64_after_64_steps": err}
+        del Cr
+    del C64, rwork
     return out
 
 

@@ -357,8 +357,11 @@ int sb_solve_batched_refined_noalloc(const sb_factor* f, const float* rhs, doubl
  *   f, rhs, x, M, ld, work, work_bytes   arrays of G entries (work/work_bytes only
  *                                        when n_refine > 0; may be NULL otherwise).
  *   rhs_dtype, x_dtype, arith            as for sb_solve_batched_ex (n_refine == 0);
- *                                        with n_refine > 0 they must be SB_F32,
- *                                        SB_F64, SB_ARITH_NATIVE (FP32 sweeps).
+ *                                        with n_refine > 0 rhs_dtype is SB_F32 or
+ *                                        SB_F64 (an FP64 right-hand side is rounded
+ *                                        to FP32 for the sweeps and used in FP64 by
+ *                                        the residual), x_dtype SB_F64 and arith
+ *                                        SB_ARITH_NATIVE (FP32 sweeps).
  *   residual_arith                       as for sb_solve_batched_refined.
  * Passes: 1 + n_refine launches in total, whatever G is.
  */
@@ -427,6 +430,23 @@ int sb_stepper_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size
  */
 int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
                    int64_t nsteps, int mode, void* work, size_t work_bytes, void* stream);
+
+/*
+ * sb_stepper_run_refined -- nsteps steps with FP32 sweeps and iterative refinement
+ * (the precision pattern of sb_solve_batched_refined applied to a time step): each
+ * step builds its right-hand side f in FP64 (one kernel, as the unfused step), then
+ * solves A C^{n+1} = f by an FP32 sweep of f rounded to FP32 into the FP64 state and
+ * n_refine passes r = f - A C (FP64 or double-float residual, residual_arith),
+ * d = A_32^{-1} r, C += d; 64-step CUDA graphs in SB_RUN_GRAPH mode.
+ *   state   device FP64, N x ld; work: sb_stepper_refined_workspace_bytes() bytes
+ *           of device memory (the FP64 f and the FP32 scratch), caller-owned.
+ * Non-periodic steppers only (SB_ERR_UNSUPPORTED otherwise); a forced stepper is
+ * rejected.  Other arguments as for sb_stepper_run.
+ */
+int sb_stepper_refined_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes);
+int sb_stepper_run_refined(sb_stepper* st, double* state, int64_t M, int64_t ld, int n_refine,
+                           sb_arith residual_arith, int64_t nsteps, int mode, void* work,
+                           size_t work_bytes, void* stream);
 
 /*
  * sb_stepper_set_forcing -- turn a periodic Cahn-Hilliard stepper into the

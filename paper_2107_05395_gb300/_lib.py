@@ -105,6 +105,9 @@ SIGNATURES = {
     "sb_stepper_run_coarsening": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, _c_i64, _vp, _vp,
                                                  ctypes.c_size_t, _vp]),
     "sb_stepper_set_forcing": (ctypes.c_int, [_vp, ctypes.c_double, _dp]),
+    "sb_stepper_refined_workspace_bytes": (ctypes.c_int, [_vp, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "sb_stepper_run_refined": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int, _c_i64,
+                                              ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "sb_stepper_run_forced": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, ctypes.c_int, _vp]),
     "sb_device_timeouts": (ctypes.c_int, [ctypes.c_int, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
@@ -462,6 +465,25 @@ def sb_stepper_run(st: Stepper, state, nsteps, arith="native", mode="graph", wor
     _check(lib().sb_stepper_run(st.handle, _dev_ptr(state), M, ld, _arith_code(arith), int(nsteps),
                                 RUN_MODES[mode] if isinstance(mode, str) else int(mode), wptr or None,
                                 wbytes, _stream_handle(stream)))
+    return state
+
+
+def sb_stepper_refined_workspace_bytes(st: Stepper, M, ld=None):
+    out = ctypes.c_size_t()
+    _check(lib().sb_stepper_refined_workspace_bytes(st.handle, M, M if ld is None else ld, ctypes.byref(out)))
+    return out.value
+
+
+def sb_stepper_run_refined(st: Stepper, state, nsteps, work, n_refine=2, residual_arith="native", mode="graph",
+                           M=None, ld=None, stream=None):
+    """Advance `state` by nsteps steps whose solves are FP32 sweeps plus n_refine
+    refinement passes with an FP64 (or double-float) residual; `work` holds
+    sb_stepper_refined_workspace_bytes() bytes on the device."""
+    M, ld = _batch_shape(state, st.N, M, ld)
+    _check(lib().sb_stepper_run_refined(st.handle, _dev_ptr(state), M, ld, int(n_refine),
+                                        _arith_code(residual_arith), int(nsteps),
+                                        RUN_MODES[mode] if isinstance(mode, str) else int(mode),
+                                        _dev_ptr(work), _nbytes(work), _stream_handle(stream)))
     return state
 
 

@@ -76,14 +76,19 @@ __device__ __forceinline__ float narrow_trunc(double v) { return double_to_df(v)
 template <bool DFRES>
 struct Residual;
 
+__device__ __forceinline__ double to_f64(float b) { return widen_f32(b); }
+__device__ __forceinline__ double to_f64(double b) { return b; }
+__device__ __forceinline__ df to_df(float b) { return {b, 0.f}; }
+__device__ __forceinline__ df to_df(double b) { return double_to_df(b); }
+
 template <>
 struct Residual<false> {  // FP64 residual: r = b - sum_k a_k x_{i+k} with FMAs
   using X = double;
   using AC = double;
   static __device__ __forceinline__ X in(double v) { return v; }
-  template <int NB>
-  static __device__ __forceinline__ float eval(const AC* a, const X* xw, float b) {
-    double r = widen_f32(b);
+  template <int NB, typename TB>
+  static __device__ __forceinline__ float eval(const AC* a, const X* xw, TB b) {
+    double r = to_f64(b);
 #pragma unroll
     for (int k = 0; k < NB; ++k) r = fma(-a[k], xw[k], r);
     return narrow_trunc(r);
@@ -95,19 +100,21 @@ struct Residual<true> {  // the same residual in double-float arithmetic
   using X = df;
   using AC = df;
   static __device__ __forceinline__ X in(double v) { return double_to_df(v); }
-  template <int NB>
-  static __device__ __forceinline__ float eval(const AC* a, const X* xw, float b) {
-    df r = {b, 0.f};
+  template <int NB, typename TB>
+  static __device__ __forceinline__ float eval(const AC* a, const X* xw, TB b) {
+    df r = to_df(b);
 #pragma unroll
     for (int k = 0; k < NB; ++k) r = DFArith::fmac(df{-a[k].h, -a[k].l}, xw[k], r);
     return r.h;
   }
 };
 
-template <int P, bool DFRES, int R>
+// TB: the stored right-hand side, FP32 (the mixed-precision solve) or FP64 (a
+// right-hand side built in FP64, e.g. by a time step).
+template <int P, bool DFRES, int R, typename TB>
 __device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
                                             const typename Residual<DFRES>::AC* arow, int N,
-                                            int64_t M, int64_t ld, const float* b, double* x,
+                                            int64_t M, int64_t ld, const TB* b, double* x,
                                             float* g, int64_t tile) {
   using RS = Residual<DFRES>;
   using X = typename RS::X;
@@ -115,7 +122,7 @@ __device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
   constexpr int NB = 2 * P + 1;
   const int64_t m = tile * 32 + (threadIdx.x & 31);
   if (m >= M) return;
-  const float* bp = b + m;
+  const TB* bp = b + m;
   double* xp = x + m;
   float* gp = g + m;
 
@@ -124,8 +131,8 @@ __device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
 #pragma unroll
   for (int k = 0; k < NB; ++k) xw[k] = RS::in(0.0);
   double xa[R], xb[R];
-  float ba[R], bb[R];
-  auto load = [&](double (&xs)[R], float (&bs)[R], int i0) {
+  TB ba[R], bb[R];
+  auto load = [&](double (&xs)[R], TB (&bs)[R], int i0) {
 #pragma unroll
     for (int j = 0; j < R; ++j)
       if (i0 + j < N) {
@@ -139,7 +146,7 @@ __device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
     xw[NB - 1] = RS::in(v);
   };
   float u1 = 0.f, u2 = 0.f;
-  auto row = [&](int i, float bi) {
+  auto row = [&](int i, TB bi) {
     const float r = RS::template eval<NB>(arow + NB * i, xw, bi);
     const float u = NativeArith<float>::step<P, false>(fw + W * i, r, u1, u2);
     gp[(int64_t)i * ld] = u;
@@ -206,9 +213,9 @@ __device__ __forceinline__ void refine_tile(const float* fw, const float* bw,
   }
 }
 
-template <int P, bool DFRES>
+template <int P, bool DFRES, typename TB>
 __global__ void __launch_bounds__(512)
-grouped_refine_kernel(const __grid_constant__ Groups<float, float, double> a) {
+grouped_refine_kernel(const __grid_constant__ Groups<float, TB, double> a) {
   using AC = typename Residual<DFRES>::AC;
   constexpr int W = P + 1;
   constexpr int NB = 2 * P + 1;
@@ -224,8 +231,8 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, float, double> a) {
   const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
   for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
        tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
-    refine_tile<P, DFRES, kRows>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g],
-                                 a.work[g], tile);
+    refine_tile<P, DFRES, kRows, TB>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g],
+                                     a.work[g], tile);
 }
 
 // ------------------------------------------------------------------ host
@@ -301,13 +308,13 @@ int launch_grouped_sweep(const std::vector<const sb_factor*>& f, Op op,
   return cuda_check(cudaGetLastError(), "grouped sweep launch");
 }
 
-template <int P, bool DFRES>
+template <int P, bool DFRES, typename TB>
 int launch_grouped_refine(const std::vector<const sb_factor*>& f, const std::vector<const void*>& rhs,
                           const std::vector<void*>& x, const std::vector<int64_t>& M,
                           const std::vector<int64_t>& ld, const std::vector<void*>& work,
                           cudaStream_t stream) {
   using AC = typename Residual<DFRES>::AC;
-  Groups<float, float, double> a{};
+  Groups<float, TB, double> a{};
   a.G = (int)f.size();
   size_t smem = 0;
   for (int g = 0; g < a.G; ++g) {
@@ -317,14 +324,14 @@ int launch_grouped_refine(const std::vector<const sb_factor*>& f, const std::vec
     a.M[g] = M[g];
     a.ld[g] = ld[g];
     a.ntiles[g] = (M[g] + 31) / 32;
-    a.rhs[g] = static_cast<const float*>(rhs[g]);
+    a.rhs[g] = static_cast<const TB*>(rhs[g]);
     a.x[g] = static_cast<double*>(x[g]);
     a.work[g] = static_cast<float*>(work[g]);
     smem = std::max(smem, (size_t)(2 * P + 1) * f[g]->N * sizeof(AC) +
                               (size_t)2 * (P + 1) * f[g]->N * sizeof(float));
   }
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
-  auto k = grouped_refine_kernel<P, DFRES>;
+  auto k = grouped_refine_kernel<P, DFRES, TB>;
   int total = 0;
   SB_TRY(resident_ctas(k, f[0]->device, smem, &total));
   const int grid = plan(a, f, total);
@@ -353,7 +360,7 @@ size_t dsize(sb_dtype t) { return t == SB_F64 ? 8 : (t == SB_F32 ? 4 : 0); }
 int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void* const* x,
                  const int64_t* M, const int64_t* ld, sb_dtype rt, sb_dtype xt, sb_arith arith,
                  int n_refine, sb_arith res_arith, void* const* work, const size_t* work_bytes,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, bool fp32_sweeps) {
   if (G < 1 || G > kMaxGroups)
     return fail(SB_ERR_INVALID_ARG, "number of groups must be in [1, %d]", kMaxGroups);
   if (!fs || !rhs || !x || !M || !ld) return fail(SB_ERR_INVALID_ARG, "NULL array argument");
@@ -398,9 +405,9 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
     Ms.push_back(M[g]);
     lds.push_back(ld[g]);
   }
-  if (n_refine > 0 && (rt != SB_F32 || xt != SB_F64 || arith != SB_ARITH_NATIVE))
+  if (n_refine > 0 && (xt != SB_F64 || arith != SB_ARITH_NATIVE))
     return fail(SB_ERR_UNSUPPORTED,
-                "refinement takes FP32 right-hand sides, FP64 solutions and FP32 sweeps (native)");
+                "refinement takes FP32 or FP64 right-hand sides, FP64 solutions and FP32 sweeps (native)");
   if (n_refine > 0)
     for (int g = 0; g < G; ++g)
       if (rhs[g] == x[g]) return fail(SB_ERR_INVALID_ARG, "refinement needs x separate from rhs");
@@ -424,6 +431,9 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
       rc = grouped_sweep_dispatch<DFArith, float, double>(f, OP_PRIMAL, r, xs, Ms, lds, cdf.data(), stream);
     else
       rc = fail(SB_ERR_UNSUPPORTED, "double-float sweeps write FP64 solutions");
+  } else if (rt == SB_F64 && xt == SB_F64 && (n_refine > 0 || fp32_sweeps)) {
+    // mixed precision with an FP64 right-hand side: FP32 sweeps of b rounded to FP32
+    rc = grouped_sweep_dispatch<NativeArith<float>, double, double>(f, OP_PRIMAL, r, xs, Ms, lds, c32.data(), stream);
   } else if (rt == SB_F64 && xt == SB_F64) {
     rc = grouped_sweep_dispatch<NativeArith<double>, double, double>(f, OP_PRIMAL, r, xs, Ms, lds, c64.data(), stream);
   } else if (rt == SB_F32 && xt == SB_F32) {
@@ -435,12 +445,22 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
   }
   SB_TRY(rc);
   for (int k = 0; k < n_refine; ++k) {
-    if (f[0]->P == 1)
-      rc = res_arith == SB_ARITH_DF32 ? launch_grouped_refine<1, true>(f, r, xs, Ms, lds, ws, stream)
-                                      : launch_grouped_refine<1, false>(f, r, xs, Ms, lds, ws, stream);
-    else
-      rc = res_arith == SB_ARITH_DF32 ? launch_grouped_refine<2, true>(f, r, xs, Ms, lds, ws, stream)
-                                      : launch_grouped_refine<2, false>(f, r, xs, Ms, lds, ws, stream);
+    const bool dfr = res_arith == SB_ARITH_DF32;
+    if (rt == SB_F64) {
+      if (f[0]->P == 1)
+        rc = dfr ? launch_grouped_refine<1, true, double>(f, r, xs, Ms, lds, ws, stream)
+                 : launch_grouped_refine<1, false, double>(f, r, xs, Ms, lds, ws, stream);
+      else
+        rc = dfr ? launch_grouped_refine<2, true, double>(f, r, xs, Ms, lds, ws, stream)
+                 : launch_grouped_refine<2, false, double>(f, r, xs, Ms, lds, ws, stream);
+    } else {
+      if (f[0]->P == 1)
+        rc = dfr ? launch_grouped_refine<1, true, float>(f, r, xs, Ms, lds, ws, stream)
+                 : launch_grouped_refine<1, false, float>(f, r, xs, Ms, lds, ws, stream);
+      else
+        rc = dfr ? launch_grouped_refine<2, true, float>(f, r, xs, Ms, lds, ws, stream)
+                 : launch_grouped_refine<2, false, float>(f, r, xs, Ms, lds, ws, stream);
+    }
     SB_TRY(rc);
   }
   return SB_OK;
@@ -572,9 +592,9 @@ int noalloc_refined(const sb_factor* f, const float* rhs, double* x, int64_t M, 
     a.work[0] = scratch;
     const size_t smem = (size_t)(2 * P + 1) * N * 8 + (size_t)2 * (P + 1) * N * sizeof(float);
     if (res == SB_ARITH_DF32)
-      SB_TRY(launch_one_group(grouped_refine_kernel<P, true>, a, N, M, smem, f->device, stream));
+      SB_TRY(launch_one_group(grouped_refine_kernel<P, true, float>, a, N, M, smem, f->device, stream));
     else
-      SB_TRY(launch_one_group(grouped_refine_kernel<P, false>, a, N, M, smem, f->device, stream));
+      SB_TRY(launch_one_group(grouped_refine_kernel<P, false, float>, a, N, M, smem, f->device, stream));
   }
   return SB_OK;
 }

@@ -123,6 +123,8 @@ struct sb_stepper {
   std::mutex mu;
   std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
   std::map<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t>, cudaGraphExec_t> forced_graphs;
+  // graphs of the FP32 + refinement steps: (state, work, M, ld, n_refine * 2 + residual mode)
+  std::map<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t, int>, cudaGraphExec_t> refined_graphs;
 };
 
 namespace sb {
@@ -179,4 +181,11 @@ int launch_partitioned(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_
 int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype, void* x,
                  sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, const SweepShape& shape,
                  cudaStream_t stream);
+// refine.cu: grouped (and refined) solves, G groups in one launch per pass.
+// fp32_sweeps: an FP64 right-hand side is swept in FP32 even with n_refine == 0 (by
+// default an FP64 right-hand side gets FP64 sweeps unless refinement is asked for).
+int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void* const* x,
+                 const int64_t* M, const int64_t* ld, sb_dtype rt, sb_dtype xt, sb_arith arith,
+                 int n_refine, sb_arith res_arith, void* const* work, const size_t* work_bytes,
+                 cudaStream_t stream, bool fp32_sweeps = false);
 }  // namespace sb

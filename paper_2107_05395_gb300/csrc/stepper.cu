@@ -549,6 +549,14 @@ int step_fused(const sb_stepper* st, double* state, int64_t M, int64_t ld, sb_ar
 }  // namespace
 }  // namespace sb
 
+namespace sb {
+namespace {
+// the FP64 right-hand side of a refined step, rounded up so the FP32 scratch after it
+// stays 16-byte aligned
+size_t refined_f_bytes(size_t elems) { return ((elems * sizeof(double) + 255) / 256) * 256; }
+}  // namespace
+}  // namespace sb
+
 using namespace sb;
 
 extern "C" {
@@ -671,6 +679,7 @@ void sb_stepper_destroy(sb_stepper* st) {
     DeviceGuard g(st->fac->device);
     for (auto& kv : st->graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : st->forced_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : st->refined_graphs) cudaGraphExecDestroy(kv.second);
     if (st->g64) cudaFree(st->g64);
     if (st->r64) cudaFree(st->r64);
     if (st->rdf) cudaFree(st->rdf);
@@ -760,6 +769,96 @@ int sb_stepper_run_forced(sb_stepper* st, double* state, const double* amp, int6
   int64_t n = 0;
   for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
   for (; n < nsteps; ++n) SB_TRY(one_step_forced(st, state, amp, M, ld, s));
+  return SB_OK;
+}
+
+int sb_stepper_refined_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes) {
+  clear_error();
+  if (!st || !bytes) return fail(SB_ERR_INVALID_ARG, "NULL argument");
+  if (M < 0 || ld < M) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  const size_t elems = (size_t)((st->N - 1) * ld + M);
+  *bytes = refined_f_bytes(elems) + elems * sizeof(float);
+  return SB_OK;
+}
+
+int sb_stepper_run_refined(sb_stepper* st, double* state, int64_t M, int64_t ld, int n_refine,
+                           sb_arith residual_arith, int64_t nsteps, int mode, void* work,
+                           size_t work_bytes, void* stream) {
+  clear_error();
+  if (!st) return fail(SB_ERR_INVALID_ARG, "stepper is NULL");
+  if (st->forced) return fail(SB_ERR_INVALID_ARG, "a forced stepper runs through sb_stepper_run_forced");
+  if (st->fac->periodic)
+    return fail(SB_ERR_UNSUPPORTED, "the refined steps do not support periodic ends");
+  if (nsteps < 0) return fail(SB_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (n_refine < 0 || n_refine > 16) return fail(SB_ERR_INVALID_ARG, "n_refine must be in [0, 16]");
+  if (residual_arith != SB_ARITH_NATIVE && residual_arith != SB_ARITH_DF32)
+    return fail(SB_ERR_INVALID_ARG, "unknown residual arithmetic mode %d", (int)residual_arith);
+  if (mode != SB_RUN_GRAPH && mode != SB_RUN_DIRECT)
+    return fail(SB_ERR_INVALID_ARG, "refined runs support SB_RUN_GRAPH and SB_RUN_DIRECT");
+  const sb_factor* f = st->fac;
+  DeviceGuard g(f->device);
+  SB_TRY(g.rc);
+  if (M < 0 || ld < M || ld < 1) return fail(SB_ERR_INVALID_ARG, "bad M or ld");
+  if (M == 0 || nsteps == 0) return SB_OK;
+  const size_t elems = (size_t)((f->N - 1) * ld + M);
+  const size_t need = refined_f_bytes(elems) + elems * sizeof(float);
+  SB_TRY(check_device_range(state, elems * sizeof(double), sizeof(double), f->device, "state"));
+  if (work == nullptr || work_bytes < need)
+    return fail(SB_ERR_INVALID_ARG, "the refined run needs a workspace of %zu bytes", need);
+  SB_TRY(check_device_range(work, need, 16, f->device, "work"));
+  SB_TRY(check_alias(state, elems * sizeof(double), work, need, "state", "work"));
+  double* fbuf = static_cast<double*>(work);
+  void* scratch = static_cast<char*>(work) + refined_f_bytes(elems);
+  const size_t sbytes = elems * sizeof(float);
+  cudaStream_t s = (cudaStream_t)stream;
+  // one step: f = B C + E phi(C) in FP64 (the unfused right-hand side), then C = A^{-1} f
+  // by FP32 sweeps of f and n_refine passes r = f - A C (residual in FP64 or
+  // double-float), d = A_32^{-1} r, C += d
+  auto step = [&]() -> int {
+    SB_TRY(one_rhs<NativeArith<double>>(st, st->r64, state, fbuf, M, ld, s));
+    const void* r = fbuf;
+    void* x = state;
+    return solve_groups(1, &f, &r, &x, &M, &ld, SB_F64, SB_F64, SB_ARITH_NATIVE, n_refine,
+                        residual_arith, &scratch, &sbytes, s, /*fp32_sweeps=*/true);
+  };
+  bool capturing = false;
+  if (mode == SB_RUN_GRAPH && s != nullptr) {
+    cudaStreamCaptureStatus cs;
+    SB_CUDA(cudaStreamIsCapturing(s, &cs));
+    capturing = (cs != cudaStreamCaptureStatusNone);
+  }
+  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
+    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(step());
+    return SB_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(st->mu);
+    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(work), M, ld,
+                               n_refine * 2 + (residual_arith == SB_ARITH_DF32 ? 1 : 0));
+    auto it = st->refined_graphs.find(key);
+    if (it != st->refined_graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t graph = nullptr;
+      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int rc = SB_OK;
+      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = step();
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc != SB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      SB_CUDA(e);
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SB_CUDA(e);
+      st->refined_graphs[key] = exec;
+    }
+  }
+  int64_t n = 0;
+  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
+  for (; n < nsteps; ++n) SB_TRY(step());
   return SB_OK;
 }
 

@@ -18,8 +18,11 @@ struct Conv<NativeArith<T>, T> {
   static __device__ __forceinline__ T out(T v) { return v; }
 };
 template <>
-struct Conv<NativeArith<float>, double> {  // FP32 arithmetic, FP64 output (exact widening)
-  static __device__ __forceinline__ double out(float v) { return widen_f32(v); }
+struct Conv<NativeArith<float>, double> {  // FP32 arithmetic on FP64 data
+  // input: the FP64 value truncated to FP32 with integer operations (the leading
+  // part of its double-float split; a refined solve corrects the rest)
+  static __device__ __forceinline__ float in(double v) { return double_to_df(v).h; }
+  static __device__ __forceinline__ double out(float v) { return widen_f32(v); }  // exact widening
 };
 template <>
 struct Conv<DFArith, double> {
