@@ -45,3 +45,15 @@ def max_over_ranks(x: float, device=None, group=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def batch_mean_in_rank_order(local_mean: torch.Tensor, local_count: int, total_count: int,
+                             group=None) -> torch.Tensor:
+    """The mean over every system of the batch of a per-step statistic that each rank
+    has averaged over its own ``local_count`` systems (the coarsening length of
+    section 5.3, one value per step): sum_r count_r * mean_r / total, combined in
+    rank order so every rank gets the same bits."""
+    if total_count < 1:
+        raise ValueError("the batch is empty")
+    weighted = local_mean.to(torch.float64) * float(local_count)
+    return sum_in_rank_order(weighted, group) / float(total_count)

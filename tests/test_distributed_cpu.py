@@ -80,3 +80,48 @@ def test_two_gloo_ranks_sum_the_parameter_gradient_in_rank_order():
     _, _, dp_all = rollout.adjoint(rollout.diffusion_problem(N, 0.5), synth.rhs_uniform(seed=1, N=N, M=M),
                                    synth.rhs_uniform(seed=2, N=N, M=M), T)
     assert abs(expect - float(np.sum(dp_all))) <= 1e-14 * abs(expect)
+
+
+def _ell_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from oracle import matrices, steppers
+    from paper_2107_05395_gb300.distributed import batch_mean_in_rank_order, shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    N, M, steps = 24, 11, 6
+    C = synth.rhs_uniform(seed=3, N=N, M=M, lo=-0.5, hi=0.5)
+    start, count = shard(M, rank, world)
+    A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, 0.05 * 0.5))
+    Cl = C[:, start:start + count]
+    ell = []
+    for _ in range(steps):
+        Cl = steppers.ch_step_periodic(A, Cl, 0.05)
+        ell.append(steppers.coarsening_length(Cl))
+    series = batch_mean_in_rank_order(torch.tensor(ell, dtype=torch.float64), count, M)
+    out[rank] = series.numpy().tolist()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_average_the_coarsening_length():
+    import synth
+    from oracle import matrices, steppers
+
+    world = 2
+    port = _free_port()
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_ell_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    assert out[0] == out[1]  # the same bits on every rank
+    N, M, steps = 24, 11, 6
+    C = synth.rhs_uniform(seed=3, N=N, M=M, lo=-0.5, hi=0.5)
+    A = steppers.SharedPentaPeriodic(*matrices.ch_matrix_periodic(N, 0.05 * 0.5))
+    ref = []
+    for _ in range(steps):
+        C = steppers.ch_step_periodic(A, C, 0.05)
+        ref.append(steppers.coarsening_length(C))
+    assert np.max(np.abs(np.array(out[0]) - np.array(ref)) / np.array(ref)) <= 1e-14
