@@ -205,7 +205,9 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
  *                        With 128-thread CTAs it is the FP64 form for latency-bound
  *                        batches: tiles of 8 systems cut into 16 chunks of 8/16/32 rows
  *                        (32 <= N <= 512), FP64 rhs and x, native arithmetic, the
- *                        boundary system solved by block Thomas; same fallback.
+ *                        boundary system solved by cyclic reduction when every CTA
+ *                        has one tile (latency-bound batches), else by block
+ *                        Thomas; same fallback.
  */
 typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
 

@@ -454,16 +454,18 @@ inline std::vector<double> transpose_diagonals(int PB, int N, const double* diag
   return t;
 }
 
-// FP64 image for the small-tile FP64 kernel (scalar records, block Thomas factors).
+// FP64 image for the small-tile FP64 kernel (scalar records, both forms of the
+// boundary solve: block Thomas factors and the cyclic-reduction matrices).
 // Sections, each starting on a multiple of 4 elements:
 //   fwd  P L rows of FW = (PB == 2 ? 4 : 2): F0, F1[, F2, 0];  bwd  P L rows of PB: B1[, B2]
 //   cor  P L rows of Q: W_0[, W_1], V_0[, V_1]
 //   E    K x PB x Q;  H  K x Q x Q;  J  K x Q x PB  (row-major, boundary-major)
+//   T0, M  as in PartLayout (entry-major, P boundary slots, NL levels)
 struct PartLayoutT {
-  int fwd, bwd, cor, E, H, J, total;
+  int fwd, bwd, cor, E, H, J, T0, M, total;
 };
 
-inline PartLayoutT part_layout_thomas(int PB, int L, int P) {
+inline PartLayoutT part_layout_thomas(int PB, int L, int P, int NL) {
   const int Q = 2 * PB, FW = PB == 2 ? 4 : 2, NP = P * L, K = P - 1;
   PartLayoutT l;
   int o = 0;
@@ -479,13 +481,17 @@ inline PartLayoutT part_layout_thomas(int PB, int L, int P) {
   o = round4(o + K * Q * Q);
   l.J = o;
   o = round4(o + K * Q * PB);
-  l.total = o;
+  l.T0 = o;
+  o = round4(o + Q * Q * P);
+  l.M = o;
+  o += NL * (Q * Q + 2 * Q * PB) * P;
+  l.total = round4(o);
   return l;
 }
 
 inline std::vector<double> partition_image_thomas(const Partition& p) {
   const int PB = p.PB, W = PB + 1, FW = PB == 2 ? 4 : 2, Q = 2 * PB, NP = p.P * p.L;
-  const PartLayoutT l = part_layout_thomas(PB, p.L, p.P);
+  const PartLayoutT l = part_layout_thomas(PB, p.L, p.P, p.NL);
   std::vector<double> img(l.total, 0.0);
   for (int i = 0; i < NP; ++i) {
     for (int k = 0; k < W; ++k) img[l.fwd + i * FW + k] = p.fw[(size_t)W * i + k];
@@ -498,6 +504,10 @@ inline std::vector<double> partition_image_thomas(const Partition& p) {
   std::copy(p.E.begin(), p.E.end(), img.begin() + l.E);
   std::copy(p.H.begin(), p.H.end(), img.begin() + l.H);
   std::copy(p.J.begin(), p.J.end(), img.begin() + l.J);
+  // the cyclic-reduction sections, laid out as in partition_image
+  const std::vector<double> pcr = partition_image(p);
+  const PartLayout lp = part_layout(PB, p.L, p.P, p.NL);
+  std::copy(pcr.begin() + lp.T0, pcr.begin() + lp.total, img.begin() + l.T0);
   return img;
 }
 

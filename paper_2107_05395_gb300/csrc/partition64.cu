@@ -8,9 +8,12 @@
 //   - lane l of warp w owns system l % 8 of the tile and chunk 4w + l / 8, and loads
 //     its chunk's rows straight into registers (8 lanes read one 64 B row segment);
 //   - each chunk is swept forward and back with its own factors (y_c = A_c^{-1} b_c);
-//   - the chunk heads and tails go to shared memory and 8 threads, one per system,
-//     solve the block-tridiagonal boundary system by block Thomas (the cheapest form
-//     on the FP64 pipe; its factors E, H, J depend on A only);
+//   - the chunk heads and tails go to shared memory and the block-tridiagonal
+//     boundary system is solved either by block Thomas, 8 threads (one per system)
+//     walking the 15 boundaries (the least FP64 work; factors E, H, J from A alone),
+//     or, when every CTA has a single tile so the solve is latency-bound, by cyclic
+//     reduction with all 128 threads: 16 lanes per system, lane k holding boundary
+//     k, four levels with warp shuffles (matrices T0, M from A alone);
 //   - every thread corrects its rows, x_c = y_c - W_c lam_c - V_c rho_c, and stores
 //     them.
 // The partition image is staged into shared memory once per CTA; CTAs are
@@ -34,10 +37,12 @@ struct alignas(sizeof(T) * n) Row {
   T v[n];
 };
 
+constexpr int kLevels = 4;  // cyclic-reduction levels for kChunks - 1 = 15 boundaries
+
 template <int PB, int L>
 __global__ void __launch_bounds__(kThreads)
 part64_kernel(const double* __restrict__ image, PartLayoutT lay, int N, int64_t M, int64_t ld,
-              const double* rhs, double* x, int64_t ntiles) {
+              const double* rhs, double* x, int64_t ntiles, bool pcr) {
   constexpr int Q = 2 * PB, FW = PB == 2 ? 4 : 2, K = kChunks - 1;
   using RF = Row<double, FW>;
   using RB = Row<double, PB>;
@@ -109,8 +114,64 @@ part64_kernel(const double* __restrict__ image, PartLayoutT lay, int N, int64_t 
       tips[(c * Q + PB + u) * kPS + s] = y[L - PB + u];  // tail of chunk c
     }
     __syncthreads();
-    // boundary system by block Thomas, one thread per system
-    if (threadIdx.x < kPS) {
+    if (pcr) {
+      // boundary system by cyclic reduction: lanes 16 ss .. 16 ss + 15 serve system
+      // ss, lane k boundary k (slot 15 holds none)
+      const int ss = threadIdx.x >> 4, k = threadIdx.x & 15;
+      double d[Q];
+      {
+        double r[Q];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          r[u] = k < K ? tips[(k * Q + PB + u) * kPS + ss] : 0.0;         // tail of chunk k
+          r[PB + u] = k < K ? tips[((k + 1) * Q + u) * kPS + ss] : 0.0;   // head of chunk k+1
+        }
+        const double* T0 = img + lay.T0 + k;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          double t = 0.0;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) t = fma(T0[(i * Q + j) * kChunks], r[j], t);
+          d[i] = t;
+        }
+      }
+      const double* Mb = img + lay.M + k;
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l) {
+        const int st = 1 << l;
+        double dl[PB], dr[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          dl[u] = __shfl_up_sync(0xffffffffu, d[u], st, 16);
+          dr[u] = __shfl_down_sync(0xffffffffu, d[PB + u], st, 16);
+        }
+        const bool has_l = k >= st, has_r = k + st < K;
+        const double* M0 = Mb;
+        const double* M1 = Mb + Q * Q * kChunks;
+        const double* M2 = M1 + Q * PB * kChunks;
+        double nd[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          double t = 0.0;
+#pragma unroll
+          for (int j = 0; j < Q; ++j) t = fma(M0[(i * Q + j) * kChunks], d[j], t);
+#pragma unroll
+          for (int j = 0; j < PB; ++j) {
+            if (has_l) t = fma(-M1[(i * PB + j) * kChunks], dl[j], t);
+            if (has_r) t = fma(-M2[(i * PB + j) * kChunks], dr[j], t);
+          }
+          nd[i] = t;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = nd[i];
+        Mb += (Q * Q + 2 * Q * PB) * kChunks;
+      }
+      if (k < K) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) zb[(k * Q + i) * kPS + ss] = d[i];
+      }
+    } else if (threadIdx.x < kPS) {
+      // boundary system by block Thomas, one thread per system
       const int ss = threadIdx.x;
       double qp[Q];
 #pragma unroll
@@ -185,7 +246,7 @@ part64_kernel(const double* __restrict__ image, PartLayoutT lay, int N, int64_t 
 template <int PB, int L>
 int launch(const sb_factor* f, const double* image, const void* rhs, void* x, int64_t M, int64_t ld,
            const SweepShape& shape, cudaStream_t stream) {
-  const PartLayoutT lay = part_layout_thomas(PB, L, kChunks);
+  const PartLayoutT lay = part_layout_thomas(PB, L, kChunks, kLevels);
   constexpr int Q = 2 * PB;
   const size_t smem = ((size_t)lay.total + (size_t)(2 * kChunks - 1) * Q * kPS) * sizeof(double);
   if (smem > (size_t)kMaxDynSmem)
@@ -196,9 +257,12 @@ int launch(const sb_factor* f, const double* image, const void* rhs, void* x, in
   if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
   const int64_t ntiles = (M + kPS - 1) / kPS;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
+  // one tile per CTA: the boundary solve is on the critical path of the whole launch,
+  // so take the parallel form; otherwise the one with the least FP64 work
+  const bool pcr = ntiles <= grid;
   k<<<(unsigned)grid, kThreads, smem, stream>>>(image, lay, (int)f->N, M, ld,
                                                 static_cast<const double*>(rhs), static_cast<double*>(x),
-                                                ntiles);
+                                                ntiles, pcr);
   return cuda_check(cudaGetLastError(), "partitioned FP64 solve launch");
 }
 

@@ -182,13 +182,18 @@ MATS64 = {
     "ch_N256": (lambda: matrices.ch_matrix(256, 0.0166), 333),
     "tri_random_N40_padded": (lambda: synth.random_tri_diagonals(seed=16, N=40), 65),
     "penta_random_N100_empty_chunks": (lambda: synth.random_penta_diagonals(seed=17, N=100), 9),
+    # more tiles than resident CTAs: the block-Thomas form of the boundary solve (the
+    # cases above have one tile per CTA and take cyclic reduction)
+    "tri_diffusion_N256_M40000_thomas": (lambda: matrices.diffusion_matrix(256, 0.5), 40000),
+    "hinged_N512_M30000_thomas": (lambda: matrices.hyperdiffusion_matrix(512, 0.25), 30000),
 }
 
 
 @pytest.mark.parametrize("name", list(MATS64))
 def test_partitioned_fp64_matches_oracle(env, name):
     """The FP64 form against the FP64 oracle at the FP64 tolerance, A and A^T, ragged
-    tiles of 8 systems, padding columns untouched, then in place."""
+    tiles of 8 systems, padding columns untouched, then in place; both boundary
+    solvers (cyclic reduction for one tile per CTA, block Thomas beyond)."""
     sb, torch = env
     make, M = MATS64[name]
     diags = make()
