@@ -149,3 +149,20 @@ def test_product_matrix_builder_rejects_bad_input(sb):
         sb.sb_build_matrix(99, 8, 0.1)
     with pytest.raises(sb.SbError):
         sb.sb_build_matrix("hinged", 8, float("inf"))
+
+
+def test_stepper_entry_points_reject_null_handles(sb):
+    """The stepper entry points added for the forced scheme, the refined steps and the
+    coarsening run refuse a NULL stepper (or NULL outputs) on the host."""
+    L = sb.lib()
+    z = np.zeros(8)
+    p = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    n = ctypes.c_size_t()
+    assert L.sb_stepper_set_forcing(None, 0.1, p) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_stepper_run_forced(None, None, None, 8, 8, 1, 0, None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_stepper_refined_workspace_bytes(None, 8, 8, ctypes.byref(n)) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_stepper_run_refined(None, None, 8, 8, 2, 0, 1, 0, None, 0, None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_stepper_run_coarsening(None, None, 8, 8, 0, 1, None, None, 0, None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_factor_shared_penta_periodic(3, p, p, p, p, p, ctypes.byref(ctypes.c_void_p())) \
+        == sb.SB_ERR_INVALID_ARG  # N < 5
+    assert sb.sb_last_error()
