@@ -272,7 +272,8 @@ static int upload_factor(sb_factor* f) {
       f->part_NL[v] = part.NL;
     }
   }
-  // FP64 block-Thomas images of the small-tile FP64 partitioned solve: kPart64Chunks
+  // FP64 images (block-Thomas factors and cyclic-reduction matrices) of the
+  // small-tile FP64 partitioned solve: kPart64Chunks
   // chunks of the shortest L in {8, 16, 32} that covers N, for N >= 32
   {
     int L64 = 0;
@@ -288,6 +289,7 @@ static int upload_factor(sb_factor* f) {
         }
         Partition part;
         if (!build_partition(f->P, (int)N, d, L64, kPart64Chunks, part)) continue;
+        if (part.NL != kPart64Levels) continue;  // (cannot happen for 16 chunks)
         const std::vector<double> img = partition_image_thomas(part);
         SB_CUDA(cudaMalloc(&f->part64_img[o], img.size() * sizeof(double)));
         SB_CUDA(cudaMemcpy(f->part64_img[o], img.data(), img.size() * sizeof(double),

@@ -37,7 +37,9 @@ struct alignas(sizeof(T) * n) Row {
   T v[n];
 };
 
-constexpr int kLevels = 4;  // cyclic-reduction levels for kChunks - 1 = 15 boundaries
+constexpr int kLevels = kPart64Levels;  // cyclic-reduction levels for kChunks - 1 boundaries
+static_assert(kChunks == kPart64Chunks && (1 << kLevels) >= kChunks - 1 && (1 << (kLevels - 1)) < kChunks - 1,
+              "the image's chunk and level counts must match the kernel's");
 
 template <int PB, int L>
 __global__ void __launch_bounds__(kThreads)

@@ -165,6 +165,7 @@ int stepper_step(const sb_stepper* st, const double* src, double* dst, int64_t M
 // The small-tile FP64 partitioned solve (partition64.cu): 128-thread CTAs, 16 chunks.
 constexpr int kPart64Threads = 128;
 constexpr int kPart64Chunks = 16;
+constexpr int kPart64Levels = 4;  // cyclic-reduction levels for its 15 chunk boundaries
 bool partitioned64_applies(const sb_factor* f, Op op, sb_dtype rhs_dtype, sb_dtype x_dtype,
                            int64_t M, sb_arith arith);
 int launch_partitioned64(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M, int64_t ld,
