@@ -47,4 +47,19 @@ int h_partition_image(int PB, int N, const double* diag, int L, int P, double* o
   return l.total;
 }
 
+// The FP64 small-tile image: block-Thomas factors and cyclic-reduction sections;
+// layout = fwd, bwd, cor, E, H, J, T0, M, total.
+int h_partition_image_thomas(int PB, int N, const double* diag, int L, int P, double* out, int cap,
+                             int* layout) {
+  Partition p;
+  if (!build_partition(PB, N, diag, L, P, p)) return -1;
+  const PartLayoutT l = part_layout_thomas(PB, L, P, p.NL);
+  const std::vector<double> img = partition_image_thomas(p);
+  if ((int)img.size() != l.total || l.total > cap) return -1;
+  for (int k = 0; k < l.total; ++k) out[k] = img[k];
+  const int lv[9] = {l.fwd, l.bwd, l.cor, l.E, l.H, l.J, l.T0, l.M, l.total};
+  for (int k = 0; k < 9; ++k) layout[k] = lv[k];
+  return l.total;
+}
+
 }  // extern "C"

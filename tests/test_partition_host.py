@@ -38,6 +38,8 @@ def H(tmp_path_factory):
                                     ctypes.c_int, ctypes.c_long, dp, dp, ctypes.c_int]
     L.h_partition_image.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
                                     ctypes.c_int, ip]
+    L.h_partition_image_thomas.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
+                                           ctypes.c_int, ip]
     return L
 
 
@@ -172,3 +174,29 @@ def test_zero_pivot_is_reported(H):
     # too few chunks to cover the rows
     dm2 = _diag_major(synth.random_penta_diagonals(10, 40))
     assert H.h_partition_solve(2, 40, _dp(dm2), 8, 4, 0, 1, _dp(b0), _dp(x), 0) == -1
+
+
+@pytest.mark.parametrize("PB,N,L", [(1, 256, 16), (2, 500, 32), (2, 100, 8)])
+def test_fp64_image_carries_both_boundary_solvers(H, PB, N, L):
+    """The FP64 small-tile image (16 chunks) holds the same chunk rows as the
+    cyclic-reduction image, the block-Thomas factors, and the cyclic-reduction
+    sections T0 / M copied entry for entry (the kernel uses either)."""
+    P = 16
+    diags = synth.random_penta_diagonals(seed=N, N=N) if PB == 2 else synth.random_tri_diagonals(seed=N, N=N)
+    dm = _diag_major(diags)
+    a = np.zeros(200000)
+    la = (ctypes.c_int * 6)()
+    na = H.h_partition_image(PB, N, _dp(dm), L, P, _dp(a), a.size, la)
+    b = np.zeros(200000)
+    lb = (ctypes.c_int * 9)()
+    nb = H.h_partition_image_thomas(PB, N, _dp(dm), L, P, _dp(b), b.size, lb)
+    assert na > 0 and nb > 0
+    fwd, bwd, cor, T0, M, total = list(la)
+    tf, tb, tc, E, Hs, J, tT0, tM, ttotal = list(lb)
+    assert (fwd, bwd, cor) == (tf, tb, tc)
+    assert E == T0 and np.array_equal(a[:T0], b[:E])                # chunk rows
+    assert np.array_equal(a[T0:total], b[tT0:tT0 + (total - T0)])    # T0 and the levels
+    assert tM - tT0 == M - T0 and ttotal - tT0 == total - T0
+    Q = 2 * PB
+    assert E >= tc and Hs - E >= (P - 1) * PB * Q and J - Hs >= (P - 1) * Q * Q and tT0 - J >= (P - 1) * Q * PB
+    assert np.any(b[E:Hs] != 0) and np.any(b[Hs:J] != 0)
