@@ -9,9 +9,10 @@ travelling-wave forced Cahn-Hilliard step built on it (section 6.1):
 * mirroring the grid swaps the left- and right-biased derivatives and flips the sign;
 * a planted mistake (swapped ideal weights) breaks the quintic exactness;
 * with no advection and no forcing the forced step is the plain periodic CH step;
-* the paper's printed forced convergence study (Table 4): E_256 = 0.0013 under the
-  reading of Table 3 (`tests/golden/paper_table4.json`); the stencil biased the
-  other way gives about 6.8e-4, so this also fixes the side."""
+* the paper's printed forced convergence study (Table 4): E_256 = 0.0013 and
+  E_512 = 1.8e-4 under the reading of Table 3 (`tests/golden/paper_table4.json`);
+  the stencil biased the other way gives E_256 of about 6.8e-4, so this also fixes
+  the side."""
 import json
 import math
 import os
@@ -134,8 +135,15 @@ def forced_run(N):
     return C[:, 0]
 
 
-def test_table4_first_row():
+@pytest.fixture(scope="module")
+def forced_runs():
+    return {N: forced_run(N) for N in (128, 256, 512)}
+
+
+def test_table4_first_rows(forced_runs):
+    """E_256 = 0.0013 and E_512 = 1.8e-4 as printed (two significant digits each)."""
     rows = {int(r[0]): r for r in json.load(open(GOLDEN))["rows"]}
-    r128, r256 = forced_run(128), forced_run(256)
-    E256 = steppers.convergence_error(r128, r256)
+    E256 = steppers.convergence_error(forced_runs[128], forced_runs[256])
+    E512 = steppers.convergence_error(forced_runs[256], forced_runs[512])
     assert abs(E256 - rows[256][1]) <= 0.5e-4, E256  # printed 0.0013
+    assert abs(E512 - rows[512][1]) <= 0.5e-5, E512  # printed 1.8e-4
