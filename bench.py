@@ -791,7 +791,9 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e2e_ms, device="cuda")
 
     extras = {}
-    if not args.no_extras:
+    # the paper-workload extras run on one GPU (a multi-GPU run measures the scaling
+    # of the headline step only, unless extras are named explicitly)
+    if not args.no_extras and (world == 1 or OPTIONS["extras"]):
         for name, fn in (("tri_latency", extra_tri_latency), ("multigroup_refine", extra_multigroup),
                          ("cahn_hilliard", extra_cahn_hilliard), ("adjoint_rollout", extra_rollout),
                          ("paper_table1_periodic_cn", extra_periodic_cn), ("coarsening", extra_coarsening),
