@@ -1,14 +1,19 @@
 """Builds the in-tree shared library ``libsbsolve.so`` for sm_103a with nvcc.
 
 Each translation unit under ``csrc/`` is compiled in parallel into ``_build/``
-(git-ignored) and linked into ``paper_2107_05395_gb300/libsbsolve.so``.  A
-library newer than every source and header is reused.  Run as
+(git-ignored) and linked into ``paper_2107_05395_gb300/libsbsolve.so``.  The
+library is reused only when it was linked from exactly the current sources,
+headers, compiler flags and host architecture: a SHA-256 of all of them is written
+beside it (``libsbsolve.so.sha256``) at link time and compared on the next build,
+so a stale binary with a newer file time is never taken for a fresh one.  Run as
 ``python -m paper_2107_05395_gb300.build`` or through ``__graft_entry__.build()``.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -19,6 +24,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbsolve.so")
+LIB_HASH = LIB + ".sha256"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
@@ -43,11 +49,23 @@ def _inputs():
     return files
 
 
+def inputs_hash() -> str:
+    """SHA-256 over every input's name and contents, the flags and the host machine."""
+    h = hashlib.sha256()
+    h.update(repr((ARCH, COMMON, platform.machine(), platform.system())).encode())
+    for f in sorted(_inputs()):
+        h.update(os.path.relpath(f, ROOT).encode() + b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_HASH)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _inputs())
+    with open(LIB_HASH) as fh:
+        return fh.read().strip() == inputs_hash()
 
 
 def _compile(src: str, verbose: bool) -> str:
@@ -64,9 +82,10 @@ def _compile(src: str, verbose: bool) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libsbsolve.so unless it is already newer than its inputs."""
+    """Compile and link libsbsolve.so unless it was linked from the current inputs."""
     if not force and up_to_date():
         return LIB
+    digest = inputs_hash()
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
@@ -77,6 +96,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB_HASH + ".tmp", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(LIB_HASH + ".tmp", LIB_HASH)
     return LIB
 
 

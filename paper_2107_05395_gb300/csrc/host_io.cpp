@@ -7,12 +7,13 @@
 #include <algorithm>
 #include <mutex>
 
+#include "host_layout.h"
 #include "sb_internal.h"
 
 namespace sb {
 namespace {
 
-constexpr int kSlots = 3;
+constexpr int kSlots = kHostSlots;
 constexpr int kMaxDev = 64;
 
 struct DevStreams {
@@ -65,7 +66,7 @@ int sb_host_workspace_bytes(const sb_factor* f, int64_t M, int64_t chunk_systems
   if (esize(rhs_dtype) == 0 || esize(x_dtype) == 0) return fail(SB_ERR_INVALID_ARG, "unknown dtype");
   const int64_t c = chunk_systems > 0 ? std::min(chunk_systems, std::max<int64_t>(M, 1))
                                        : auto_chunk(std::max<int64_t>(M, 1), std::min(esize(rhs_dtype), esize(x_dtype)));
-  *bytes = (size_t)kSlots * (size_t)f->N * (size_t)c * (esize(rhs_dtype) + esize(x_dtype));
+  *bytes = (size_t)kSlots * host_slot_bytes(f->N, c, esize(rhs_dtype), esize(x_dtype));
   return SB_OK;
 }
 
@@ -105,7 +106,7 @@ int sb_solve_batched_host(const sb_factor* f, int transpose, const void* rhs_hos
   for (int k = 0; k < kSlots; ++k) SB_CUDA(cudaStreamWaitEvent(ds->s[k], ds->start, 0));
 
   const int64_t N = f->N;
-  const size_t slot_bytes = (size_t)N * (size_t)C * (rs + xs);
+  const size_t slot = host_slot_bytes(N, C, rs, xs), x_off = host_slot_x_offset(N, C, rs);
   const Op op = transpose ? OP_ADJOINT : OP_PRIMAL;
   const SweepShape shape = shape_for(f, arith, rhs_dtype, x_dtype);
   int64_t chunk = 0;
@@ -113,9 +114,9 @@ int sb_solve_batched_host(const sb_factor* f, int transpose, const void* rhs_hos
     const int64_t Mc = std::min(C, M - m0);
     const int k = (int)(chunk % kSlots);
     cudaStream_t s = ds->s[k];
-    char* base = static_cast<char*>(work) + (size_t)k * slot_bytes;
+    char* base = static_cast<char*>(work) + (size_t)k * slot;
     void* d_rhs = base;
-    void* d_x = base + (size_t)N * (size_t)C * rs;
+    void* d_x = base + x_off;
     SB_CUDA(cudaMemcpy2DAsync(d_rhs, (size_t)Mc * rs, static_cast<const char*>(rhs_host) + (size_t)m0 * rs,
                               (size_t)ld * rs, (size_t)Mc * rs, (size_t)N, cudaMemcpyHostToDevice, s));
     SB_TRY(launch_sweep(f, op, d_rhs, rhs_dtype, d_x, x_dtype, Mc, Mc, arith, shape, s));

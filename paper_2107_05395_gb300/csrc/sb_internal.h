@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <list>
 #include <map>
 #include <mutex>
 #include <string>
@@ -68,6 +69,38 @@ struct SweepShape {
 constexpr int kPartVariants = 2;
 inline int part_chunks(int v) { return 16 << v; }
 
+// Captured CUDA graphs keyed by the pointers and sizes they were captured with.  A
+// caller that passes fresh buffers on every run would otherwise make the cache grow
+// without bound, so at most kCap executables are kept and the least recently used
+// one is destroyed first (CUDA frees an executable that is still running when it
+// completes).  Not thread-safe: the owner holds its lock around every call.
+template <typename K>
+struct GraphCache {
+  static constexpr size_t kCap = 8;
+  std::list<std::pair<K, cudaGraphExec_t>> items;  // most recently used first
+
+  cudaGraphExec_t find(const K& key) {
+    for (auto it = items.begin(); it != items.end(); ++it)
+      if (it->first == key) {
+        items.splice(items.begin(), items, it);
+        return items.front().second;
+      }
+    return nullptr;
+  }
+  void put(const K& key, cudaGraphExec_t exec) {
+    items.emplace_front(key, exec);
+    while (items.size() > kCap) {
+      cudaGraphExecDestroy(items.back().second);
+      items.pop_back();
+    }
+  }
+  void clear() {
+    for (auto& kv : items) cudaGraphExecDestroy(kv.second);
+    items.clear();
+  }
+  size_t size() const { return items.size(); }
+};
+
 }  // namespace sb
 
 struct sb_factor {
@@ -121,10 +154,12 @@ struct sb_stepper {
   double adv = 0.0;
   double* g64 = nullptr;  // device forcing profile, N values
   std::mutex mu;
-  std::map<std::tuple<uintptr_t, int64_t, int64_t, int, int>, cudaGraphExec_t> graphs;
-  std::map<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t>, cudaGraphExec_t> forced_graphs;
-  // graphs of the FP32 + refinement steps: (state, work, M, ld, n_refine * 2 + residual mode)
-  std::map<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t, int>, cudaGraphExec_t> refined_graphs;
+  // captured step graphs: fused steps (state, M, ld, arith, steps), forced steps
+  // (state, amp, M, ld) and FP32 + refinement steps (state, work, M, ld,
+  // n_refine * 2 + residual mode)
+  sb::GraphCache<std::tuple<uintptr_t, int64_t, int64_t, int, int>> graphs;
+  sb::GraphCache<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t>> forced_graphs;
+  sb::GraphCache<std::tuple<uintptr_t, uintptr_t, int64_t, int64_t, int>> refined_graphs;
 };
 
 namespace sb {

@@ -554,6 +554,51 @@ namespace {
 // the FP64 right-hand side of a refined step, rounded up so the FP32 scratch after it
 // stays 16-byte aligned
 size_t refined_f_bytes(size_t elems) { return ((elems * sizeof(double) + 255) / 256) * 256; }
+
+// Runs `nsteps` steps of `step` on stream s: as replays of a captured graph of
+// kGraphSteps steps (cached in `cache` under `key`) and the remainder launched
+// directly.  Direct launches are used for every step when the mode asks for them,
+// on the legacy stream, inside a caller's capture, or for fewer than kGraphSteps
+// steps.
+template <typename K, typename Step>
+int run_graphed(sb_stepper* st, GraphCache<K>& cache, const K& key, int mode, int64_t nsteps,
+                cudaStream_t s, Step step) {
+  bool capturing = false;
+  if (mode == SB_RUN_GRAPH && s != nullptr) {
+    cudaStreamCaptureStatus cs;
+    SB_CUDA(cudaStreamIsCapturing(s, &cs));
+    capturing = (cs != cudaStreamCaptureStatusNone);
+  }
+  if (mode != SB_RUN_GRAPH || s == nullptr || capturing || nsteps < kGraphSteps) {
+    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(step());
+    return SB_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(st->mu);
+    exec = cache.find(key);
+    if (exec == nullptr) {
+      cudaGraph_t graph = nullptr;
+      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int rc = SB_OK;
+      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = step();
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc != SB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      SB_CUDA(e);
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SB_CUDA(e);
+      cache.put(key, exec);
+    }
+  }
+  int64_t n = 0;
+  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
+  for (; n < nsteps; ++n) SB_TRY(step());
+  return SB_OK;
+}
 }  // namespace
 }  // namespace sb
 
@@ -677,9 +722,9 @@ void sb_stepper_destroy(sb_stepper* st) {
   if (!st) return;
   if (st->fac) {
     DeviceGuard g(st->fac->device);
-    for (auto& kv : st->graphs) cudaGraphExecDestroy(kv.second);
-    for (auto& kv : st->forced_graphs) cudaGraphExecDestroy(kv.second);
-    for (auto& kv : st->refined_graphs) cudaGraphExecDestroy(kv.second);
+    st->graphs.clear();
+    st->forced_graphs.clear();
+    st->refined_graphs.clear();
     if (st->g64) cudaFree(st->g64);
     if (st->r64) cudaFree(st->r64);
     if (st->rdf) cudaFree(st->rdf);
@@ -707,7 +752,6 @@ int sb_stepper_set_forcing(sb_stepper* st, double adv, const double* profile) {
   // the advection coefficient is a launch argument, so they are rebuilt
   SB_CUDA(cudaDeviceSynchronize());
   SB_CUDA(cudaMemcpy(st->g64, profile, (size_t)N * sizeof(double), cudaMemcpyHostToDevice));
-  for (auto& kv : st->forced_graphs) cudaGraphExecDestroy(kv.second);
   st->forced_graphs.clear();
   st->adv = adv;
   st->forced = true;
@@ -732,44 +776,9 @@ int sb_stepper_run_forced(sb_stepper* st, double* state, const double* amp, int6
   SB_TRY(check_device_range(amp, (size_t)M * sizeof(double), sizeof(double), f->device, "amp"));
   SB_TRY(check_alias(state, bytes, amp, (size_t)M * sizeof(double), "state", "amp"));
   cudaStream_t s = (cudaStream_t)stream;
-  bool capturing = false;
-  if (mode == SB_RUN_GRAPH && s != nullptr) {
-    cudaStreamCaptureStatus cs;
-    SB_CUDA(cudaStreamIsCapturing(s, &cs));
-    capturing = (cs != cudaStreamCaptureStatusNone);
-  }
-  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
-    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(one_step_forced(st, state, amp, M, ld, s));
-    return SB_OK;
-  }
-  cudaGraphExec_t exec = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(st->mu);
-    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(amp), M, ld);
-    auto it = st->forced_graphs.find(key);
-    if (it != st->forced_graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      int rc = SB_OK;
-      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = one_step_forced(st, state, amp, M, ld, s);
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
-      if (rc != SB_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-      }
-      SB_CUDA(e);
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      SB_CUDA(e);
-      st->forced_graphs[key] = exec;
-    }
-  }
-  int64_t n = 0;
-  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
-  for (; n < nsteps; ++n) SB_TRY(one_step_forced(st, state, amp, M, ld, s));
-  return SB_OK;
+  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(amp), M, ld);
+  return run_graphed(st, st->forced_graphs, key, mode, nsteps, s,
+                     [&]() { return one_step_forced(st, state, amp, M, ld, s); });
 }
 
 int sb_stepper_refined_workspace_bytes(const sb_stepper* st, int64_t M, int64_t ld, size_t* bytes) {
@@ -821,45 +830,9 @@ int sb_stepper_run_refined(sb_stepper* st, double* state, int64_t M, int64_t ld,
     return solve_groups(1, &f, &r, &x, &M, &ld, SB_F64, SB_F64, SB_ARITH_NATIVE, n_refine,
                         residual_arith, &scratch, &sbytes, s, /*fp32_sweeps=*/true);
   };
-  bool capturing = false;
-  if (mode == SB_RUN_GRAPH && s != nullptr) {
-    cudaStreamCaptureStatus cs;
-    SB_CUDA(cudaStreamIsCapturing(s, &cs));
-    capturing = (cs != cudaStreamCaptureStatusNone);
-  }
-  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
-    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(step());
-    return SB_OK;
-  }
-  cudaGraphExec_t exec = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(st->mu);
-    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(work), M, ld,
-                               n_refine * 2 + (residual_arith == SB_ARITH_DF32 ? 1 : 0));
-    auto it = st->refined_graphs.find(key);
-    if (it != st->refined_graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      int rc = SB_OK;
-      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = step();
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
-      if (rc != SB_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-      }
-      SB_CUDA(e);
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      SB_CUDA(e);
-      st->refined_graphs[key] = exec;
-    }
-  }
-  int64_t n = 0;
-  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
-  for (; n < nsteps; ++n) SB_TRY(step());
-  return SB_OK;
+  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(work), M, ld,
+                                   n_refine * 2 + (residual_arith == SB_ARITH_DF32 ? 1 : 0));
+  return run_graphed(st, st->refined_graphs, key, mode, nsteps, s, [&]() { return step(); });
 }
 
 int sb_stepper_run_coarsening(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arith arith,
@@ -952,45 +925,10 @@ int sb_stepper_run(sb_stepper* st, double* state, int64_t M, int64_t ld, sb_arit
     return SB_OK;
   }
 
-  bool capturing = false;
-  if (mode == SB_RUN_GRAPH && s != nullptr) {
-    cudaStreamCaptureStatus cs;
-    SB_CUDA(cudaStreamIsCapturing(s, &cs));
-    capturing = (cs != cudaStreamCaptureStatusNone);
-  }
-  if (mode == SB_RUN_DIRECT || s == nullptr || capturing || nsteps < kGraphSteps) {
-    for (int64_t n = 0; n < nsteps; ++n) SB_TRY(step_fused(st, state, M, ld, arith, s));
-    return SB_OK;
-  }
-  // graph of kGraphSteps fused steps, replayed; the remainder launched directly
-  cudaGraphExec_t exec = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(st->mu);
-    auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), M, ld, (int)arith, kGraphSteps);
-    auto it = st->graphs.find(key);
-    if (it != st->graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      SB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      int rc = SB_OK;
-      for (int n = 0; n < kGraphSteps && rc == SB_OK; ++n) rc = step_fused(st, state, M, ld, arith, s);
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
-      if (rc != SB_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-      }
-      SB_CUDA(e);
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      SB_CUDA(e);
-      st->graphs[key] = exec;
-    }
-  }
-  int64_t n = 0;
-  for (; n + kGraphSteps <= nsteps; n += kGraphSteps) SB_CUDA(cudaGraphLaunch(exec, s));
-  for (; n < nsteps; ++n) SB_TRY(step_fused(st, state, M, ld, arith, s));
-  return SB_OK;
+  // graphs of kGraphSteps fused steps, replayed; the remainder launched directly
+  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), M, ld, (int)arith, kGraphSteps);
+  return run_graphed(st, st->graphs, key, mode, nsteps, s,
+                     [&]() { return step_fused(st, state, M, ld, arith, s); });
 }
 
 }  // extern "C"

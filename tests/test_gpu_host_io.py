@@ -88,3 +88,26 @@ def test_chunking_does_not_change_the_bits(env, kind):
         sb.sb_solve_batched_host(fac, rhs, rhs, work, transpose=transpose, M=M)  # in place, direct
         torch.cuda.synchronize()
         assert np.array_equal(rhs.numpy()[:, :M], outs[0][:, :M])
+
+
+@pytest.mark.parametrize("N,chunk", [(5, 3), (201, 7), (77, 0)])
+def test_fp32_rhs_fp64_solution_with_odd_slot_sizes(env, N, chunk):
+    """FP32 right-hand sides with FP64 solutions: with an odd N * chunk the FP64 part
+    of each workspace slot follows an odd number of FP32 values, so this case checks
+    the slot layout's alignment on the device (chunk 0 picks M itself when M is small)."""
+    sb, torch = env
+    M, ld = 29, 31
+    diags = synth.random_penta_diagonals(seed=12, N=N)
+    fac = sb.sb_factor_shared_penta(*diags)
+    host = synth.rhs_uniform(seed=13, N=N, M=M, ld=ld, dtype=np.float32, pad_value=0.5)
+    rhs = torch.from_numpy(host.copy()).pin_memory()
+    x = torch.full((N, ld), 0.5, dtype=torch.float64).pin_memory()
+    work = torch.empty(sb.sb_host_workspace_bytes(fac, M, chunk, rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F64),
+                       dtype=torch.uint8, device="cuda")
+    sb.sb_solve_batched_host(fac, rhs, x, work, chunk_systems=chunk, M=M)
+    torch.cuda.synchronize()
+    fo = banded.penta_factor(*diags)
+    ref = banded.penta_solve(*fo, host[:, :M].astype(np.float64))
+    # FP32 sweeps of an exactly widened FP32 right-hand side
+    assert np.max(relerr_per_system(x.numpy()[:, :M], ref)) <= 2e-5
+    assert np.all(x.numpy()[:, M:] == 0.5)
