@@ -190,8 +190,10 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
  *   SB_ALGO_PARTITIONED  this library's own (no counterpart in the paper): a CTA
  *                        keeps a tile of 32 systems on chip (the tile arrives by TMA
  *                        while the previous one is solved), cut into 16 chunks of
- *                        16/32/64 rows (512 threads) or 32 chunks of 8/16/32 rows (1024
- *                        threads); every chunk is swept with its own factors and the
+ *                        16/32/64 rows (512 threads, one warp per chunk; or 256 threads,
+ *                        half a warp per chunk with two systems per thread, the default
+ *                        for FP32 rhs) or 32 chunks of 8/16/32 rows (1024 threads);
+ *                        every chunk is swept with its own factors and the
  *                        chunks are joined through the small system of their boundary
  *                        values, solved by parallel cyclic reduction (a SPIKE-type
  *                        decomposition, exact up to rounding, whose spikes and reduction
@@ -214,9 +216,9 @@ typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
 /*
  * Launch shape of a batched solve.
  *   threads             threads per CTA: a multiple of 32 in [32, 512] for
- *                       SB_ALGO_SEQUENTIAL; 512 (16 chunks) or 1024 (32 chunks) for
- *                       SB_ALGO_PARTITIONED with FP32 rhs (one warp per chunk), 128 for
- *                       its FP64 form.
+ *                       SB_ALGO_SEQUENTIAL; 256 (16 chunks, two systems per thread),
+ *                       512 (16 chunks) or 1024 (32 chunks) for SB_ALGO_PARTITIONED
+ *                       with FP32 rhs, 128 for its FP64 form.
  *   ctas_per_sm         cap on resident CTAs per SM (0 = as many as fit; 0 or 1 for
  *                       SB_ALGO_PARTITIONED, which fits one).
  *   systems_per_thread  1 or 2 for SB_ALGO_SEQUENTIAL (each thread interleaves that

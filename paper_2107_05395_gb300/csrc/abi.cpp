@@ -245,11 +245,12 @@ static int upload_factor(sb_factor* f) {
   SB_CUDA(cudaMemcpy(f->arow64, arow.data(), arow.size() * sizeof(double), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->arowdf, arowdf.data(), arowdf.size() * sizeof(float), cudaMemcpyHostToDevice));
   // images of the partitioned solve of A and A^T (FP32) for each variant: chunks of
-  // the shortest L that covers N (16/32/64 rows for 16 chunks, 8/16/32 for 32), N >= 64
+  // the shortest L that covers N (16/32/64 rows for 16 chunks, 8/16/32 for 32), N >= 64;
+  // variant 2 holds variant 0's rows with each pair of chunks interleaved
   for (int v = 0; v < kPartVariants && !f->periodic; ++v) {
     const int P = part_chunks(v);
     int L = 0;
-    const int lens[3] = {v == 0 ? 16 : 8, v == 0 ? 32 : 16, v == 0 ? 64 : 32};
+    const int lens[3] = {v == 1 ? 8 : 16, v == 1 ? 16 : 32, v == 1 ? 32 : 64};
     for (int cand : lens)
       if (L == 0 && (int64_t)cand * P >= N) L = cand;
     if (N < 64 || L == 0) continue;
@@ -262,7 +263,7 @@ static int upload_factor(sb_factor* f) {
       }
       Partition part;
       if (!build_partition(f->P, (int)N, d, L, P, part)) continue;  // a zero pivot
-      const std::vector<double> img = partition_image(part);
+      const std::vector<double> img = v == 2 ? partition_image_paired(part) : partition_image(part);
       std::vector<float> img32(img.size());
       for (size_t k = 0; k < img.size(); ++k) img32[k] = (float)img[k];
       SB_CUDA(cudaMalloc(&f->part_img[o][v], img32.size() * sizeof(float)));

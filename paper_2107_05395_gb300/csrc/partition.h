@@ -443,6 +443,26 @@ inline std::vector<double> partition_image(const Partition& p) {
   return img;
 }
 
+// The same image with the rows of each pair of chunks (2w, 2w + 1) interleaved, for
+// the kernel whose warp w holds both chunks (half a warp each): in the fwd, bwd and
+// cor sections row j of chunk c sits at padded row (c / 2) 2L + 2j + c % 2, so the
+// two half-warps read neighbouring records; the reduction sections are unchanged.
+// Needs an even number of chunks.
+inline std::vector<double> partition_image_paired(const Partition& p) {
+  const PartLayout l = part_layout(p.PB, p.L, p.P, p.NL);
+  const std::vector<double> plain = partition_image(p);
+  std::vector<double> img = plain;
+  const int FW = p.PB == 2 ? 4 : 2, Q = 2 * p.PB, L = p.L;
+  for (int c = 0; c < p.P; ++c)
+    for (int j = 0; j < L; ++j) {
+      const int from = c * L + j, to = (c / 2) * 2 * L + 2 * j + c % 2;
+      for (int e = 0; e < FW; ++e) img[l.fwd + to * FW + e] = plain[l.fwd + from * FW + e];
+      for (int e = 0; e < p.PB; ++e) img[l.bwd + to * p.PB + e] = plain[l.bwd + from * p.PB + e];
+      for (int e = 0; e < Q; ++e) img[l.cor + to * Q + e] = plain[l.cor + from * Q + e];
+    }
+  return img;
+}
+
 // Diagonals of A^T in the same diagonal-major format: A^T(i, i+o) = A(i+o, i).
 inline std::vector<double> transpose_diagonals(int PB, int N, const double* diag) {
   std::vector<double> t((size_t)(2 * PB + 1) * N, 0.0);

@@ -64,10 +64,11 @@ struct SweepShape {
   int algo = SB_ALGO_SEQUENTIAL;  // sequential sweeps or the partitioned solve
 };
 
-// Partitioned-solve variants: variant v cuts the rows into part_chunks(v) chunks,
-// one warp each (CTAs of 512 or 1024 threads).
-constexpr int kPartVariants = 2;
-inline int part_chunks(int v) { return 16 << v; }
+// Partitioned-solve variants: variant v cuts the rows into part_chunks(v) chunks:
+// 0 = 16 chunks, one warp each (512 threads); 1 = 32 chunks (1024 threads); 2 = 16
+// chunks, half a warp each with two systems per thread (256 threads, paired image).
+constexpr int kPartVariants = 3;
+inline int part_chunks(int v) { return v == 1 ? 32 : 16; }
 
 // Captured CUDA graphs keyed by the pointers and sizes they were captured with.  A
 // caller that passes fresh buffers on every run would otherwise make the cache grow
@@ -114,8 +115,8 @@ struct sb_factor {
   double* arow64 = nullptr;  // device: A row by row, (2P+1) entries per row (offsets -P..P)
   // device images (FP32) of the partitioned solve (partition.h) of A and A^T per
   // variant v (part_chunks(v) chunks of part_L[v] rows); null where it does not apply
-  float* part_img[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  int part_L[2] = {0, 0}, part_NL[2] = {0, 0};
+  float* part_img[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int part_L[3] = {0, 0, 0}, part_NL[3] = {0, 0, 0};
   // FP64 images (block Thomas form) of the small-tile FP64 partitioned solve of A and
   // A^T: 16 chunks of part64_L rows; null where it does not apply
   double* part64_img[2] = {nullptr, nullptr};
@@ -205,7 +206,7 @@ bool partitioned64_applies(const sb_factor* f, Op op, sb_dtype rhs_dtype, sb_dty
                            int64_t M, sb_arith arith);
 int launch_partitioned64(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M, int64_t ld,
                          const SweepShape& shape, cudaStream_t stream);
-// Variant of a partitioned shape (threads 512 -> 0, 1024 -> 1, else -1).
+// Variant of a partitioned shape (threads 512 -> 0, 1024 -> 1, 256 -> 2, else -1).
 int part_variant(int threads);
 bool partitioned_applies(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype,
                          sb_dtype x_dtype, int64_t M, int64_t ld, sb_arith arith, int threads);

@@ -36,7 +36,8 @@ SweepShape shape_for(const sb_factor* f, sb_arith arith, sb_dtype rt, sb_dtype x
   // does not apply)
   if (arith == SB_ARITH_NATIVE && rt == SB_F32 && (f->part_img[0][0] || f->part_img[1][0])) {
     SweepShape s;
-    s.threads = 512;
+    // two systems per thread (variant 2) where the factor has its image
+    s.threads = (f->part_img[0][2] || f->part_img[1][2]) ? 256 : 512;
     s.ctas_per_sm = 0;
     s.spt = 1;
     s.algo = SB_ALGO_PARTITIONED;
@@ -78,7 +79,7 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
       return fail(SB_ERR_INVALID_ARG, "systems_per_thread must be 1 or 2");
   } else {
     if (part_variant(shape->threads) < 0 && shape->threads != kPart64Threads)
-      return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 128, 512 or 1024 threads per CTA");
+      return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 128, 256, 512 or 1024 threads per CTA");
     if (shape->systems_per_thread != 1 || shape->ctas_per_sm > 1)
       return fail(SB_ERR_INVALID_ARG,
                   "the partitioned solve takes systems_per_thread = 1 and ctas_per_sm 0 or 1");
@@ -132,7 +133,7 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
     s.algo = SB_ALGO_PARTITIONED;
     cands.push_back(s);
   }
-  for (int threads : {512, 1024})
+  for (int threads : {256, 512, 1024})
     if (partitioned_applies(f, op, rhs, rhs_dtype, x_dtype, M, ld, arith, threads)) {
       SweepShape s;
       s.threads = threads;

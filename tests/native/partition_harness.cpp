@@ -47,6 +47,16 @@ int h_partition_image(int PB, int N, const double* diag, int L, int P, double* o
   return l.total;
 }
 
+// The paired image (partition_image_paired); same layout as h_partition_image.
+int h_partition_image_paired(int PB, int N, const double* diag, int L, int P, double* out, int cap) {
+  Partition p;
+  if (!build_partition(PB, N, diag, L, P, p)) return -1;
+  const std::vector<double> img = partition_image_paired(p);
+  if ((int)img.size() > cap) return -1;
+  for (size_t k = 0; k < img.size(); ++k) out[k] = img[k];
+  return (int)img.size();
+}
+
 // The FP64 small-tile image: block-Thomas factors and cyclic-reduction sections;
 // layout = fwd, bwd, cor, E, H, J, T0, M, total.
 int h_partition_image_thomas(int PB, int N, const double* diag, int L, int P, double* out, int cap,

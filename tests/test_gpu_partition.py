@@ -22,7 +22,8 @@ TOL32 = 2e-5
 CANARY = 7.0
 PART = (512, 0, 1, 1)  # threads, ctas_per_sm, systems_per_thread, SB_ALGO_PARTITIONED (16 chunks)
 PART32 = (1024, 0, 1, 1)  # 32 chunks
-VARIANTS = {"16chunks": PART, "32chunks": PART32}
+PAIRS = (256, 0, 1, 1)  # 16 chunks, two systems per thread
+VARIANTS = {"16chunks": PART, "32chunks": PART32, "pairs": PAIRS}
 
 
 @pytest.fixture(scope="module")
@@ -98,6 +99,56 @@ def test_partitioned_ragged_batches_and_in_place(env, M, variant):
     out = to_host(d).astype(np.float64)
     assert np.max(relerr_per_system(out[:, :M], oracle(diags, rhs[:, :M].astype(np.float64), False))) <= TOL32
     assert np.all(out[:, M:] == CANARY)
+    assert sb.sb_device_timeouts(0) == 0
+
+
+@pytest.mark.parametrize("kind", ["penta", "tri"])
+@pytest.mark.parametrize("in_place", [False, True])
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_partitioned_many_tiles_per_cta_every_system(env, kind, in_place, variant):
+    """Several tiles per persistent CTA (3 to 4 on a 152-SM GPU) and a ragged last
+    tile, every system against the oracle: each CTA's loads, stores and buffer swaps
+    run through more than one round, A and A^T, in place or not."""
+    sb, torch = env
+    N, M = 333, 152 * 32 * 3 + 17
+    ld = M + 3
+    diags = (synth.random_penta_diagonals if kind == "penta" else synth.random_tri_diagonals)(seed=31, N=N)
+    fac = factor(sb, diags)
+    sb.sb_shape_set(fac, VARIANTS[variant], rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32)
+    rhs = synth.rhs_normal(seed=32, N=N, M=M, ld=ld, pad_value=CANARY).astype(np.float32)
+    for adjoint in (False, True):
+        d = to_dev(rhs, torch)
+        x = d if in_place else torch.full_like(d, CANARY)
+        sb.sb_solve_batched_ex(fac, d, x, transpose=adjoint, M=M)
+        torch.cuda.synchronize()
+        out = to_host(x).astype(np.float64)
+        ref = oracle(diags, rhs[:, :M].astype(np.float64), adjoint)
+        assert np.max(relerr_per_system(out[:, :M], ref)) <= TOL32, adjoint
+        assert np.all(out[:, M:] == CANARY)
+    assert sb.sb_device_timeouts(0) == 0
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("xt", ["f32", "f64"])
+def test_partitioned_with_misaligned_solution(env, variant, xt):
+    """A solution array offset by one element from its allocation (so not aligned for
+    the two-system stores) is still written correctly, and nothing outside it."""
+    sb, torch = env
+    N, M, ld = 300, 200, 204
+    diags = synth.random_penta_diagonals(seed=33, N=N)
+    fac = factor(sb, diags)
+    xcode = sb.SB_F64 if xt == "f64" else sb.SB_F32
+    sb.sb_shape_set(fac, VARIANTS[variant], rhs_dtype=sb.SB_F32, x_dtype=xcode)
+    rhs = synth.rhs_normal(seed=34, N=N, M=M, ld=ld).astype(np.float32)
+    d = to_dev(rhs, torch)
+    base = torch.full((N * ld + 1,), CANARY, dtype=torch.float64 if xt == "f64" else torch.float32, device="cuda")
+    x = base[1:].view(N, ld)
+    sb.sb_solve_batched_ex(fac, d, x, M=M, ld=ld)
+    torch.cuda.synchronize()
+    out = to_host(x).astype(np.float64)
+    assert np.max(relerr_per_system(out[:, :M], oracle(diags, rhs[:, :M].astype(np.float64), False))) <= TOL32
+    assert np.all(out[:, M:] == CANARY) and float(base[0]) == CANARY
+    assert sb.sb_device_timeouts(0) == 0
 
 
 @pytest.mark.parametrize("variant", list(VARIANTS))
@@ -152,7 +203,7 @@ def test_fallback_where_the_partition_does_not_apply(env, case):
 def test_bad_partitioned_shapes_rejected(env):
     sb, _ = env
     fac = factor(sb, synth.random_penta_diagonals(seed=1, N=256))
-    for bad in [(256, 0, 1, 1), (1024, 2, 1, 1), (512, 0, 2, 1), (1024, 0, 1, 2)]:
+    for bad in [(384, 0, 1, 1), (1024, 2, 1, 1), (512, 0, 2, 1), (1024, 0, 1, 2)]:
         with pytest.raises(sb.SbError):
             sb.sb_shape_set(fac, bad)
 

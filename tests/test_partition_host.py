@@ -38,6 +38,8 @@ def H(tmp_path_factory):
                                     ctypes.c_int, ctypes.c_long, dp, dp, ctypes.c_int]
     L.h_partition_image.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
                                     ctypes.c_int, ip]
+    L.h_partition_image_paired.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
+                                           ctypes.c_int]
     L.h_partition_image_thomas.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp,
                                            ctypes.c_int, ip]
     return L
@@ -200,3 +202,28 @@ def test_fp64_image_carries_both_boundary_solvers(H, PB, N, L):
     Q = 2 * PB
     assert E >= tc and Hs - E >= (P - 1) * PB * Q and J - Hs >= (P - 1) * Q * Q and tT0 - J >= (P - 1) * Q * PB
     assert np.any(b[E:Hs] != 0) and np.any(b[Hs:J] != 0)
+
+
+@pytest.mark.parametrize("PB,N,L", [(2, 1000, 64), (1, 300, 32), (2, 200, 16)])
+def test_paired_image_interleaves_each_chunk_pair(H, PB, N, L):
+    """The paired image (two chunks per warp) holds exactly the rows of the plain image:
+    row j of chunk c at padded row (c // 2) 2L + 2j + c % 2 of the fwd, bwd and cor
+    sections, and the reduction sections unchanged."""
+    P = 16
+    diags = synth.random_penta_diagonals(seed=N, N=N) if PB == 2 else synth.random_tri_diagonals(seed=N, N=N)
+    dm = _diag_major(diags)
+    a = np.zeros(100000)
+    la = (ctypes.c_int * 6)()
+    na = H.h_partition_image(PB, N, _dp(dm), L, P, _dp(a), a.size, la)
+    b = np.zeros(100000)
+    nb = H.h_partition_image_paired(PB, N, _dp(dm), L, P, _dp(b), b.size)
+    assert na == nb > 0
+    fwd, bwd, cor, T0, M, total = list(la)
+    FW, Q = (4 if PB == 2 else 2), 2 * PB
+    for c in range(P):
+        for j in range(L):
+            src, dst = c * L + j, (c // 2) * 2 * L + 2 * j + c % 2
+            assert np.array_equal(b[fwd + dst * FW: fwd + dst * FW + FW], a[fwd + src * FW: fwd + src * FW + FW])
+            assert np.array_equal(b[bwd + dst * PB: bwd + dst * PB + PB], a[bwd + src * PB: bwd + src * PB + PB])
+            assert np.array_equal(b[cor + dst * Q: cor + dst * Q + Q], a[cor + src * Q: cor + src * Q + Q])
+    assert np.array_equal(a[T0:total], b[T0:total])
