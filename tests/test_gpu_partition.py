@@ -105,12 +105,16 @@ def test_partitioned_ragged_batches_and_in_place(env, M, variant):
 @pytest.mark.parametrize("kind", ["penta", "tri"])
 @pytest.mark.parametrize("in_place", [False, True])
 @pytest.mark.parametrize("variant", list(VARIANTS))
-def test_partitioned_many_tiles_per_cta_every_system(env, kind, in_place, variant):
+@pytest.mark.parametrize("N", [333, 512])
+def test_partitioned_many_tiles_per_cta_every_system(env, kind, in_place, variant, N):
     """Several tiles per persistent CTA (3 to 4 on a 152-SM GPU) and a ragged last
-    tile, every system against the oracle: each CTA's loads, stores and buffer swaps
-    run through more than one round, A and A^T, in place or not."""
+    tile, every system against the oracle: each CTA's loads and stores run through
+    more than one round, A and A^T, in place or not.  With N = 512 (16 chunks of 32
+    rows) the two-system form keeps each tile's solution in tensor memory until the
+    next tile and sends the partial last tile to its direct-store kernel; N = 333 is
+    stored directly."""
     sb, torch = env
-    N, M = 333, 152 * 32 * 3 + 17
+    M = 152 * 32 * 3 + 17
     ld = M + 3
     diags = (synth.random_penta_diagonals if kind == "penta" else synth.random_tri_diagonals)(seed=31, N=N)
     fac = factor(sb, diags)
