@@ -664,6 +664,59 @@ def extra_rollout(sb, torch, stream):
     return out
 
 
+def _r(v, digits=4):
+    """v rounded to `digits` significant digits (None and non-numbers pass through)."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}")
+    return v
+
+
+def _get(d, *keys):
+    for k in keys:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def summary(extras, fp32, df32, cpu, timeouts):
+    """Compact numeric record of every figure the workload extras report (kept at
+    the end of the JSON line): times in ms (table1 in s per 1000 steps), fractions
+    of the measured HBM peak, ratios against the plain per-step solve."""
+    ch = extras.get("cahn_hilliard", {})
+    mg = extras.get("multigroup_refine", {})
+    ro = extras.get("adjoint_rollout", {})
+    fused = _get(ch, "fused_graph_fp64", "ms_per_step")
+    out = {
+        "fp32_solve_ms": _r(fp32.get("ms_per_solve")), "fp32_hbm_frac": _r(fp32.get("hbm_frac")),
+        "fp32_kernel": fp32.get("kernel"),
+        "df32_solve_ms": _r(df32.get("ms_per_solve")),
+        "tri_latency_us": {k: _r(_get(extras, "tri_latency", k, "us_per_solve")) for k in ("native", "df32")},
+        "multigroup_ms": {k: _r(_get(mg, k, "ms_per_call"))
+                          for k in ("refine2_fp64_residual", "refine2_df32_residual", "df32_direct", "fp32_only")},
+        "multigroup_launches": {k: _get(mg, k, "launches") for k in ("refine2_fp64_residual", "refine2_df32_residual")},
+        "multigroup_max_err": _r(max([e for k in ("refine2_fp64_residual", "refine2_df32_residual")
+                                      for e in (_get(mg, k, "max_rel_err_per_group") or [])], default=None)),
+        "ch_step_ms": {k: _r(_get(ch, k, "ms_per_step"))
+                       for k in ("fused_graph_fp64", "fused_graph_df32", "unfused_fp64", "fp32_refine2_fp64res",
+                                 "fp32_refine2_df32res")},
+        "fused_vs_plain": _r(_get(ch, "unfused_fp64", "ms_per_step") / fused) if fused and
+        _get(ch, "unfused_fp64", "ms_per_step") else None,
+        "refined_vs_plain": _r(_get(ch, "fp32_refine2_fp64res", "ms_per_step") / fused) if fused and
+        _get(ch, "fp32_refine2_fp64res", "ms_per_step") else None,
+        "adjoint_vs_plain": {k: _r(_get(ro, k, "backward_vs_plain_step")) for k in ("cahn_hilliard", "diffusion")},
+        "rollout_ms": {k: [_r(_get(ro, k, "forward_ms")), _r(_get(ro, k, "backward_ms"))]
+                       for k in ("cahn_hilliard", "diffusion")},
+        "table1_s": {k: _r(_get(extras, "paper_table1_periodic_cn", k, "s_per_1000_steps"))
+                     for k in ("N64", "N256", "N1024")},
+        "cusparse_speedup": {k: _r(_get(extras, "cusparse_context", k, "speedup")) for k in ("tri", "penta")},
+        "cpu_all_cores": {"value": _r(_get(cpu, "all_cores", "value")), "cores": _get(cpu, "all_cores", "cores")}
+        if cpu else None,
+        "partition_timeouts": timeouts,
+    }
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -748,7 +801,7 @@ def run_ours(args):
     for algo, name in ((sb.SB_ALGO_SEQUENTIAL, "sequential"), (sb.SB_ALGO_PARTITIONED, "partitioned")):
         best = None
         for shp in ([(t, c, 1, algo) for t in (128, 256, 512) for c in (0, 1)] if algo == 0
-                    else [(t, 0, 1, algo) for t in (512, 1024)]):
+                    else [(t, 0, 1, algo) for t in (256, 512, 1024)]):
             sb.sb_shape_set(fac, shp, rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32)
             try:
                 t = float(np.min(time_launches(lambda: sb.sb_solve_batched(fac, rhs32, x32, stream=stream),
@@ -766,7 +819,12 @@ def run_ours(args):
     shape32 = sb.sb_autotune(fac, rhs32, x32)
     ms32 = time_launches(lambda: sb.sb_solve_batched(fac, rhs32, x32, stream=stream), stream, n32, 3)
     s32 = float(np.mean(ms32)) / 1e3
+    timeouts = sb.sb_device_timeouts(local)  # partitioned CTAs that gave up waiting (must be 0)
     fp32_extra = {"shape": list(shape32[0]), "ms_per_solve": s32 * 1e3,
+                  "kernel": ({256: "part_kernel2s (two systems per thread, stores spread through TMEM)",
+                              512: "part_kernel", 1024: "part_kernel"}.get(shape32[0][0], "part_kernel")
+                             if shape32[0][3] == sb.SB_ALGO_PARTITIONED else "sweep_kernel"),
+                  "timeouts": timeouts,
                   "batched_solves_per_s": 1.0 / s32,
                   "hbm_gbs": 8.0 * N_ROWS * M_SYS / s32 / 1e9,
                   "hbm_frac": 8.0 * N_ROWS * M_SYS / s32 / 1e9 / hbm_peak()[0],
@@ -812,6 +870,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    rates = sb.sb_measure_rates(local)  # the FP64 pipe's measured ceiling
+    fp64_peak = 2.0 * rates["fp64_fma_per_s"] / 1e12
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
     elts = N_ROWS * M_SYS
     flops = FLOPS_PER_ELT * elts
@@ -839,11 +899,13 @@ def run_ours(args):
                 "alu_fp64_equiv": {"achieved": achieved_tflops, "unit": "TFLOP/s"}}
         dtype = "f64 (double-float arithmetic)"
     else:
-        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved_tflops / fp64_peak,
                 "traffic": traffic,
                 "kernel": "sweep_kernel<NativeArith<double>,P=2> (native FP64)",
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
+                "peak_source": "measured: sb_measure_rates FP64 FMA throughput x 2 flop, this run "
+                               f"(derived nominal {FP64_PEAK_TFLOPS:.3f} TFLOP/s = 2 FMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "rates": {k: rates[k] for k in ("fp64_fma_per_s", "fp32_fma_per_s", "f64_f32_conversions_per_s")},
                 "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": achieved_gbs / hbm, "peak_source": hbm_src}}
         dtype = "f64"
@@ -874,6 +936,9 @@ def run_ours(args):
         "launch_ms": {"mean": float(np.mean(launch_ms)), "min": float(np.min(launch_ms)),
                       "max": float(np.max(launch_ms))},
     }
+    # last key of the line: the compact record of every extra's figures
+    line["summary"] = summary(extras, fp32_extra, line["extras"][f"solve_{other}"] if other == "df32" else {},
+                              cpu, timeouts)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -546,6 +546,25 @@ const char* sb_last_error(void);
 /* Library version string. */
 const char* sb_version(void);
 
+/*
+ * sb_measure_rates -- arithmetic throughputs of `device`, measured: FP64 fused
+ * multiply-adds per second (each 2 flop), FP32 fused multiply-adds per second and
+ * FP64 -> FP32 -> FP64 conversions per second (each pair counted as two).  Each is
+ * timed with CUDA events on many independent dependency chains per thread over a
+ * grid that fills every SM (middle of three launches after a warm-up), so it is
+ * the pipe's rate.  These are the ceilings the solver's FP64-bound kernels are
+ * reported against (this library's own measurement; no counterpart in the paper).
+ * Blocking; allocates and frees a small device buffer.  SB_ERR_INVALID_ARG for a
+ * NULL result, SB_ERR_CUDA on a CUDA error.
+ */
+typedef struct {
+  double fp64_fma_per_s;
+  double fp32_fma_per_s;
+  double f64_f32_conversions_per_s;
+  int sm_count;
+} sb_rates;
+int sb_measure_rates(int device, sb_rates* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,6 +110,7 @@ SIGNATURES = {
                                               ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "sb_stepper_run_forced": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, ctypes.c_int, _vp]),
     "sb_device_timeouts": (ctypes.c_int, [ctypes.c_int, _vp]),
+    "sb_measure_rates": (ctypes.c_int, [ctypes.c_int, _vp]),
     "sb_last_error": (ctypes.c_char_p, []),
     "sb_version": (ctypes.c_char_p, []),
 }
@@ -550,6 +551,19 @@ def sb_device_timeouts(device: int = 0) -> int:
     out = ctypes.c_uint()
     _check(lib().sb_device_timeouts(int(device), ctypes.byref(out)))
     return out.value
+
+
+class _Rates(ctypes.Structure):
+    _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
+                ("f64_f32_conversions_per_s", ctypes.c_double), ("sm_count", ctypes.c_int)]
+
+
+def sb_measure_rates(device: int = 0) -> dict:
+    """Measured FP64 FMA, FP32 FMA and FP64<->FP32 conversion rates of ``device``
+    (per second) and its SM count; blocking."""
+    out = _Rates()
+    _check(lib().sb_measure_rates(int(device), ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in _Rates._fields_}
 
 
 def sb_last_error() -> str:

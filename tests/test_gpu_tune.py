@@ -63,3 +63,15 @@ def test_bad_shapes_rejected(env):
                 (256, 0, 1, 7)]:
         with pytest.raises(sb.SbError):
             sb.sb_shape_set(fac, bad)
+
+
+def test_measured_rates_are_plausible(env):
+    """The arithmetic-rate probe: every rate positive, FP32 FMA well above FP64 FMA
+    (GB300's FP64 pipe is a small fraction of its FP32 pipe), and the FP64 FMA rate
+    below 2 per clock per SM at the highest SM clock (the pipe's issue limit)."""
+    sb, torch = env
+    r = sb.sb_measure_rates(0)
+    assert r["sm_count"] == torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["fp64_fma_per_s"] > 0 and r["fp32_fma_per_s"] > 0 and r["f64_f32_conversions_per_s"] > 0
+    assert r["fp32_fma_per_s"] > 10 * r["fp64_fma_per_s"]
+    assert r["fp64_fma_per_s"] <= 2.0 * r["sm_count"] * 2.2e9 * 1.05
