@@ -4,15 +4,16 @@
 //   x_0 = sweep32(b);   for k = 1..n:  r = b - A x_{k-1} (FP64, or double-float),
 //                                      d = sweep32(r),  x_k = x_{k-1} + d.
 // The factorisation of A is the FP64 one rounded to FP32 for the sweeps; the
-// residual uses A's original FP64 entries.  Each refinement pass is one kernel:
-// its forward sweep builds r_i from a window of x (rows i-P .. i+P, prefetched
-// in batches) and writes the FP32 intermediate to a caller-provided workspace
-// (x must stay intact until every residual row is built); its backward sweep
-// adds d_i to x_i.
+// residual uses A's original FP64 entries.  A correction pass's forward sweep
+// builds r_i from a window of x (rows i-P .. i+P, prefetched in batches) and
+// writes the FP32 intermediate to a caller-provided workspace (x must stay intact
+// until every residual row is built); its backward sweep adds d_i to x_i.  One
+// launch runs every pass: each warp takes a tile through the FP32 pass and all
+// correction passes before its next tile.
 //
-// Groups: several shared-LHS factors (different N) are solved by one launch per
-// pass.  The persistent CTAs are split between the groups in proportion to
-// N*M; a CTA stages its own group's coefficients once.
+// Groups: several shared-LHS factors (different N) are solved by one launch.  The
+// persistent CTAs are split between the groups in proportion to N*M; a CTA stages
+// its own group's coefficients once.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -235,6 +236,40 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, TB, double> a) {
                                      a.work[g], tile);
 }
 
+// All passes in one launch: each warp takes a tile and runs the FP32 pass (x_0 into
+// x) and then the n_refine correction passes on it, before its next tile.  Tiles are
+// independent, so no pass waits for another tile; warps drift into different passes,
+// so the FP64 residual arithmetic of some overlaps the memory phases of others.
+// Rows per prefetch batch of the fused kernel: 4 (not kRows) keeps every pass within
+// 128 registers, so two 256-thread CTAs share an SM.
+constexpr int kFusedRows = 4;
+
+template <int P, bool DFRES, typename TB>
+__global__ void __launch_bounds__(256, 2)
+grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a, int n_refine) {
+  using AC = typename Residual<DFRES>::AC;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = group_of(a.cta_begin, a.G);
+  const int N = a.N[g];
+  AC* as = reinterpret_cast<AC*>(smem_raw);  // A rows first (8-byte aligned)
+  float* cs = reinterpret_cast<float*>(as + NB * N);
+  stage(as, static_cast<const AC*>(a.arow[g]), NB * N);
+  stage(cs, a.coef[g], 2 * W * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
+  for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
+       tile < a.ntiles[g]; tile += (int64_t)ctas * nw) {
+    sweep_tile<NativeArith<float>, P, false, true, TB, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[g], a.ld[g],
+                                                                        a.rhs[g], a.x[g], tile);
+    for (int k = 0; k < n_refine; ++k)
+      refine_tile<P, DFRES, kFusedRows, TB>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g], a.work[g],
+                                       tile);
+  }
+}
+
 // ------------------------------------------------------------------ host
 
 constexpr int kThreads = 256;
@@ -309,10 +344,10 @@ int launch_grouped_sweep(const std::vector<const sb_factor*>& f, Op op,
 }
 
 template <int P, bool DFRES, typename TB>
-int launch_grouped_refine(const std::vector<const sb_factor*>& f, const std::vector<const void*>& rhs,
-                          const std::vector<void*>& x, const std::vector<int64_t>& M,
-                          const std::vector<int64_t>& ld, const std::vector<void*>& work,
-                          cudaStream_t stream) {
+int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const std::vector<const void*>& rhs,
+                                 const std::vector<void*>& x, const std::vector<int64_t>& M,
+                                 const std::vector<int64_t>& ld, const std::vector<void*>& work, int n_refine,
+                                 cudaStream_t stream) {
   using AC = typename Residual<DFRES>::AC;
   Groups<float, TB, double> a{};
   a.G = (int)f.size();
@@ -331,12 +366,12 @@ int launch_grouped_refine(const std::vector<const sb_factor*>& f, const std::vec
                               (size_t)2 * (P + 1) * f[g]->N * sizeof(float));
   }
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
-  auto k = grouped_refine_kernel<P, DFRES, TB>;
+  auto k = grouped_refined_solve_kernel<P, DFRES, TB>;
   int total = 0;
   SB_TRY(resident_ctas(k, f[0]->device, smem, &total));
   const int grid = plan(a, f, total);
-  k<<<grid, kThreads, smem, stream>>>(a);
-  return cuda_check(cudaGetLastError(), "refinement pass launch");
+  k<<<grid, kThreads, smem, stream>>>(a, n_refine);
+  return cuda_check(cudaGetLastError(), "refined solve launch");
 }
 
 template <class A, typename TI, typename TO>
@@ -422,8 +457,28 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
     c64[g] = f[g]->coef64;
     cdf[g] = reinterpret_cast<const df*>(f[g]->coefdf);
   }
-  // first pass (the whole solve when n_refine == 0)
   int rc;
+  if (n_refine > 0) {
+    // the FP32 pass and every correction pass of a tile in one launch
+    const bool dfr = res_arith == SB_ARITH_DF32;
+    if (rt == SB_F64) {
+      if (f[0]->P == 1)
+        rc = dfr ? launch_grouped_refined_solve<1, true, double>(f, r, xs, Ms, lds, ws, n_refine, stream)
+                 : launch_grouped_refined_solve<1, false, double>(f, r, xs, Ms, lds, ws, n_refine, stream);
+      else
+        rc = dfr ? launch_grouped_refined_solve<2, true, double>(f, r, xs, Ms, lds, ws, n_refine, stream)
+                 : launch_grouped_refined_solve<2, false, double>(f, r, xs, Ms, lds, ws, n_refine, stream);
+    } else {
+      if (f[0]->P == 1)
+        rc = dfr ? launch_grouped_refined_solve<1, true, float>(f, r, xs, Ms, lds, ws, n_refine, stream)
+                 : launch_grouped_refined_solve<1, false, float>(f, r, xs, Ms, lds, ws, n_refine, stream);
+      else
+        rc = dfr ? launch_grouped_refined_solve<2, true, float>(f, r, xs, Ms, lds, ws, n_refine, stream)
+                 : launch_grouped_refined_solve<2, false, float>(f, r, xs, Ms, lds, ws, n_refine, stream);
+    }
+    return rc;
+  }
+  // the whole solve in one pass
   if (arith == SB_ARITH_DF32) {
     if (rt == SB_F64 && xt == SB_F64)
       rc = grouped_sweep_dispatch<DFArith, double, double>(f, OP_PRIMAL, r, xs, Ms, lds, cdf.data(), stream);
@@ -444,25 +499,6 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
     rc = fail(SB_ERR_UNSUPPORTED, "unsupported dtype combination");
   }
   SB_TRY(rc);
-  for (int k = 0; k < n_refine; ++k) {
-    const bool dfr = res_arith == SB_ARITH_DF32;
-    if (rt == SB_F64) {
-      if (f[0]->P == 1)
-        rc = dfr ? launch_grouped_refine<1, true, double>(f, r, xs, Ms, lds, ws, stream)
-                 : launch_grouped_refine<1, false, double>(f, r, xs, Ms, lds, ws, stream);
-      else
-        rc = dfr ? launch_grouped_refine<2, true, double>(f, r, xs, Ms, lds, ws, stream)
-                 : launch_grouped_refine<2, false, double>(f, r, xs, Ms, lds, ws, stream);
-    } else {
-      if (f[0]->P == 1)
-        rc = dfr ? launch_grouped_refine<1, true, float>(f, r, xs, Ms, lds, ws, stream)
-                 : launch_grouped_refine<1, false, float>(f, r, xs, Ms, lds, ws, stream);
-      else
-        rc = dfr ? launch_grouped_refine<2, true, float>(f, r, xs, Ms, lds, ws, stream)
-                 : launch_grouped_refine<2, false, float>(f, r, xs, Ms, lds, ws, stream);
-    }
-    SB_TRY(rc);
-  }
   return SB_OK;
 }
 
