@@ -1,7 +1,8 @@
 """GPU parity of the implicit time steppers (fused right-hand side + sweeps, CUDA
 graph, and the unfused two-kernel pipeline) against the oracle's steps, and the
-Cahn-Hilliard workload (N = 256, 2^20 simulations, 2000 steps) on sampled systems
-with mass conservation checked on every system."""
+Cahn-Hilliard workload (N = 256, 2^20 simulations, 2000 steps; FP64, double-float
+and FP32 sweeps with two refinement passes) on sampled systems with mass
+conservation checked on every system."""
 import numpy as np
 import pytest
 
@@ -137,6 +138,33 @@ def test_cahn_hilliard_workload_df32(env):
     of 1e-10 (the FP64 path above holds 1e-12)."""
     sb, torch = env
     err, drift = _ch_workload(sb, torch, "df32", synth.WORKLOADS["cahn_hilliard"]["steps"])
+    assert np.max(err) <= 1e-10, (np.max(err), np.median(err))
+    assert drift <= 1e-10, drift
+
+
+def test_cahn_hilliard_workload_fp32_refined(env):
+    """The same workload with FP32 sweeps and two refinement passes per step (FP64
+    residual, sb_stepper_run_refined, graph-captured): 256 systems spread over the
+    batch within 1e-10 of the oracle's FP64 steps after 2000 steps, mass on every
+    system within 1e-10."""
+    sb, torch = env
+    w = synth.WORKLOADS["cahn_hilliard"]
+    N, M, nsteps = w["N"], w["M"], w["steps"]
+    st = sb.sb_stepper_create("cahn_hilliard", "be", "noflux", N, w["gamma"], w["dt"])
+    C0 = synth.torch_uniform(w["seed"], N, M, -w["amp"], w["amp"], torch.float64, "cuda")
+    mass0 = C0.sum(dim=0)
+    C = C0.clone()
+    work = torch.empty(sb.sb_stepper_refined_workspace_bytes(st, M), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        sb.sb_stepper_run_refined(st, C, nsteps, work, n_refine=2, residual_arith="native", stream=stream)
+    torch.cuda.synchronize()
+    del work
+    drift = ((C.sum(dim=0) - mass0).abs() / (N * C.abs().max(dim=0).values)).max().item()
+    cols = torch.as_tensor(np.linspace(0, M - 1, 256).astype(np.int64), device="cuda")
+    ref = oracle_run("cahn_hilliard", "be", "noflux", N, w["gamma"], w["dt"], to_host(C0[:, cols]), nsteps)
+    err = relerr_per_system(to_host(C[:, cols]), ref)
     assert np.max(err) <= 1e-10, (np.max(err), np.median(err))
     assert drift <= 1e-10, drift
 
