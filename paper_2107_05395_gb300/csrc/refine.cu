@@ -270,6 +270,96 @@ grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a
   }
 }
 
+// ---------------------------------------------------- refined time step
+
+// Right-hand side of a time step for one tile, in FP64, in the same order of
+// operations as the stepper's right-hand-side kernel: f_i = sum_k B_ik C_k (NB
+// values per row at offsets -(NB/2)..NB/2; f_i = C_i when NB == 0) plus, with
+// HAS_E, sum_k E_ik (C_k^3 - C_k) over offsets -1..1.  Rows outside the matrix
+// are 0.  C is read ahead in double-buffered batches of R rows.
+template <int NB, bool HAS_E, int R>
+__device__ __forceinline__ void rhs_tile(const double* rc, int N, int64_t M, int64_t ld, const double* Cin,
+                                         double* f, int64_t tile) {
+  using A = NativeArith<double>;
+  constexpr int RW = NB + (HAS_E ? 3 : 0);
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const double* cp = Cin + m;
+  double* fp = f + m;
+  auto row_c = [&](int k) { return (k >= 0 && k < N) ? ld_stream(cp + (int64_t)k * ld) : 0.0; };
+  double w[5] = {0.0, 0.0, row_c(0), row_c(1), row_c(2)};  // rows i-2 .. i+2
+  double na[R], nb[R];
+  auto load = [&](double (&b)[R], int i0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) b[j] = row_c(i0 + 3 + j);
+  };
+  auto rows = [&](const double (&b)[R], int i0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = i0 + j;
+      if (i < N) {
+        const double* rw = rc + RW * i;
+        double r;
+        if constexpr (NB > 0) {
+          r = A::mulc(rw[0], w[2 - NB / 2]);
+#pragma unroll
+          for (int k = 1; k < NB; ++k) r = A::fmac(rw[k], w[2 - NB / 2 + k], r);
+        } else {
+          r = w[2];
+        }
+        if constexpr (HAS_E) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) r = A::fmac(rw[NB + k], A::cubic(w[1 + k]), r);
+        }
+        fp[(int64_t)i * ld] = r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = w[k + 1];
+        w[4] = b[j];
+      }
+    }
+  };
+  load(na, 0);
+  for (int i0 = 0; i0 < N; i0 += 2 * R) {
+    load(nb, i0 + R);
+    rows(na, i0);
+    load(na, i0 + 2 * R);
+    rows(nb, i0 + R);
+  }
+}
+
+// One FP32 + refinement time step in one launch: each warp takes a tile of the
+// state C through its right-hand side f (FP64, into the workspace), the FP32 solve
+// of f into C (in place: the tile's C is read completely first) and n_refine
+// correction passes with the FP64 f.  a.G == 1, a.rhs[0] == f, a.x[0] == C.
+template <int P, bool DFRES, int NB, bool HAS_E>
+__global__ void __launch_bounds__(256, 2)
+refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, double* f,
+                    const double* __restrict__ rcoef, int n_refine) {
+  using AC = typename Residual<DFRES>::AC;
+  constexpr int W = P + 1;
+  constexpr int NBA = 2 * P + 1;
+  constexpr int RW = NB + (HAS_E ? 3 : 0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.N[0];
+  AC* as = reinterpret_cast<AC*>(smem_raw);          // A rows (8-byte values)
+  float* cs = reinterpret_cast<float*>(as + NBA * N);  // FP32 sweep rows
+  double* rs = reinterpret_cast<double*>(cs + 2 * W * N);  // right-hand-side rows (8-byte aligned)
+  stage(as, static_cast<const AC*>(a.arow[0]), NBA * N);
+  stage(cs, a.coef[0], 2 * W * N);
+  stage(rs, rcoef, RW * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < a.ntiles[0];
+       tile += (int64_t)gridDim.x * nw) {
+    rhs_tile<NB, HAS_E, kFusedRows>(rs, N, a.M[0], a.ld[0], a.x[0], f, tile);
+    sweep_tile<NativeArith<float>, P, false, true, double, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[0],
+                                                                                a.ld[0], f, a.x[0], tile);
+    for (int k = 0; k < n_refine; ++k)
+      refine_tile<P, DFRES, kFusedRows, double>(cs, cs + W * N, as, N, a.M[0], a.ld[0], f, a.x[0], a.work[0],
+                                                tile);
+  }
+}
+
 // ------------------------------------------------------------------ host
 
 constexpr int kThreads = 256;
@@ -300,7 +390,6 @@ int resident_ctas(K kernel, int device, size_t smem, int* total) {
 // least one CTA and no more than it has tiles for).  Returns the grid size.
 template <typename GA>
 int plan(GA& a, const std::vector<const sb_factor*>& f, int total) {
-  const int nw = kThreads / 32;
   double work = 0.0;
   for (int g = 0; g < a.G; ++g) work += (double)f[g]->N * (double)a.M[g];
   int begin = 0;
@@ -372,6 +461,52 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
   const int grid = plan(a, f, total);
   k<<<grid, kThreads, smem, stream>>>(a, n_refine);
   return cuda_check(cudaGetLastError(), "refined solve launch");
+}
+
+template <int P, bool DFRES, int NB, bool HAS_E>
+int launch_refined_step(const sb_factor* f, const double* rcoef, double* state, double* fbuf, float* scratch,
+                        int64_t M, int64_t ld, int n_refine, cudaStream_t stream) {
+  using AC = typename Residual<DFRES>::AC;
+  Groups<float, double, double> a{};
+  a.G = 1;
+  a.coef[0] = f->coef32;
+  a.arow[0] = DFRES ? static_cast<const void*>(f->arowdf) : static_cast<const void*>(f->arow64);
+  a.N[0] = (int)f->N;
+  a.M[0] = M;
+  a.ld[0] = ld;
+  a.ntiles[0] = (M + 31) / 32;
+  a.rhs[0] = fbuf;
+  a.x[0] = state;
+  a.work[0] = scratch;
+  constexpr int RW = NB + (HAS_E ? 3 : 0);
+  const size_t smem = (size_t)(2 * P + 1) * f->N * sizeof(AC) + (size_t)2 * (P + 1) * f->N * sizeof(float) +
+                      (size_t)RW * f->N * sizeof(double);
+  if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "N=%lld: the step's coefficients exceed shared memory",
+                                     (long long)f->N);
+  auto k = refined_step_kernel<P, DFRES, NB, HAS_E>;
+  int total = 0;
+  SB_TRY(resident_ctas(k, f->device, smem, &total));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ntiles[0], total));
+  a.cta_begin[0] = 0;
+  a.cta_begin[1] = (int)grid;
+  k<<<(unsigned)grid, kThreads, smem, stream>>>(a, fbuf, rcoef, n_refine);
+  return cuda_check(cudaGetLastError(), "refined step launch");
+}
+
+template <bool DFRES>
+int refined_step_dispatch(const sb_factor* f, const double* rcoef, int NB, bool has_e, double* state,
+                          double* fbuf, float* scratch, int64_t M, int64_t ld, int n_refine, cudaStream_t s) {
+  if (f->P == 1 && !has_e && NB == 0)
+    return launch_refined_step<1, DFRES, 0, false>(f, rcoef, state, fbuf, scratch, M, ld, n_refine, s);
+  if (f->P == 1 && !has_e && NB == 3)
+    return launch_refined_step<1, DFRES, 3, false>(f, rcoef, state, fbuf, scratch, M, ld, n_refine, s);
+  if (f->P == 2 && !has_e && NB == 0)
+    return launch_refined_step<2, DFRES, 0, false>(f, rcoef, state, fbuf, scratch, M, ld, n_refine, s);
+  if (f->P == 2 && !has_e && NB == 5)
+    return launch_refined_step<2, DFRES, 5, false>(f, rcoef, state, fbuf, scratch, M, ld, n_refine, s);
+  if (f->P == 2 && has_e && NB == 0)
+    return launch_refined_step<2, DFRES, 0, true>(f, rcoef, state, fbuf, scratch, M, ld, n_refine, s);
+  return fail(SB_ERR_UNSUPPORTED, "no refined step for half bandwidth %d with this right-hand side", f->P);
 }
 
 template <class A, typename TI, typename TO>
@@ -500,6 +635,15 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
   }
   SB_TRY(rc);
   return SB_OK;
+}
+
+int refined_step(const sb_factor* f, const double* rcoef, int NB, bool has_e, double* state, double* fbuf,
+                 float* scratch, int64_t M, int64_t ld, int n_refine, sb_arith residual_arith,
+                 cudaStream_t stream) {
+  if (f->periodic) return fail(SB_ERR_UNSUPPORTED, "the refined steps do not support periodic ends");
+  return residual_arith == SB_ARITH_DF32
+             ? refined_step_dispatch<true>(f, rcoef, NB, has_e, state, fbuf, scratch, M, ld, n_refine, stream)
+             : refined_step_dispatch<false>(f, rcoef, NB, has_e, state, fbuf, scratch, M, ld, n_refine, stream);
 }
 
 }  // namespace sb

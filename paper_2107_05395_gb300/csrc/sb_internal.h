@@ -225,4 +225,11 @@ int solve_groups(int G, const sb_factor* const* fs, const void* const* rhs, void
                  const int64_t* M, const int64_t* ld, sb_dtype rt, sb_dtype xt, sb_arith arith,
                  int n_refine, sb_arith res_arith, void* const* work, const size_t* work_bytes,
                  cudaStream_t stream, bool fp32_sweeps = false);
+// One FP32 + refinement time step in one launch (refine.cu): per tile, the FP64
+// right-hand side f = B C + E phi(C) of the state (rows rcoef: NB B values then, if
+// has_e, 3 E values per row) into fbuf, the FP32 solve of f into the state and
+// n_refine correction passes (residual in FP64 or double-float).
+int refined_step(const sb_factor* f, const double* rcoef, int NB, bool has_e, double* state, double* fbuf,
+                 float* scratch, int64_t M, int64_t ld, int n_refine, sb_arith residual_arith,
+                 cudaStream_t stream);
 }  // namespace sb

@@ -818,17 +818,13 @@ int sb_stepper_run_refined(sb_stepper* st, double* state, int64_t M, int64_t ld,
   SB_TRY(check_alias(state, elems * sizeof(double), work, need, "state", "work"));
   double* fbuf = static_cast<double*>(work);
   void* scratch = static_cast<char*>(work) + refined_f_bytes(elems);
-  const size_t sbytes = elems * sizeof(float);
   cudaStream_t s = (cudaStream_t)stream;
-  // one step: f = B C + E phi(C) in FP64 (the unfused right-hand side), then C = A^{-1} f
-  // by FP32 sweeps of f and n_refine passes r = f - A C (residual in FP64 or
-  // double-float), d = A_32^{-1} r, C += d
+  // one step: f = B C + E phi(C) in FP64, then C = A^{-1} f by FP32 sweeps of f and
+  // n_refine passes r = f - A C (residual in FP64 or double-float), d = A_32^{-1} r,
+  // C += d; one kernel per step, each tile taken through all of it in turn
   auto step = [&]() -> int {
-    SB_TRY(one_rhs<NativeArith<double>>(st, st->r64, state, fbuf, M, ld, s));
-    const void* r = fbuf;
-    void* x = state;
-    return solve_groups(1, &f, &r, &x, &M, &ld, SB_F64, SB_F64, SB_ARITH_NATIVE, n_refine,
-                        residual_arith, &scratch, &sbytes, s, /*fp32_sweeps=*/true);
+    return refined_step(f, st->r64, st->NB, st->has_e, state, fbuf, static_cast<float*>(scratch), M, ld,
+                        n_refine, residual_arith, s);
   };
   const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(state), reinterpret_cast<uintptr_t>(work), M, ld,
                                    n_refine * 2 + (residual_arith == SB_ARITH_DF32 ? 1 : 0));

@@ -2,6 +2,7 @@
 
     python -m paper_2107_05395_gb300.profile_case --kind penta --N 1024 --M 32768 --launches 3
     python -m paper_2107_05395_gb300.profile_case --kind forced_ch --N 512 --M 65536 --launches 3
+    python -m paper_2107_05395_gb300.profile_case --kind ch_step --step refined --N 256 --M 65536 --launches 3
 
 Everything goes through the C ABI; inputs are seeded N(0, 1) drawn on the device.
 The default case keeps the inputs above the L2 size (so DRAM counters mean
@@ -18,7 +19,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["tri", "penta", "forced_ch"], default="penta")
+    ap.add_argument("--kind", choices=["tri", "penta", "forced_ch", "ch_step"], default="penta")
+    ap.add_argument("--step", choices=["fp64", "refined"], default="fp64",
+                    help="ch_step: the fused FP64 step or the FP32 + 2 refinements step")
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--M", type=int, default=32768)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -50,6 +53,20 @@ def main():
         sb.sb_stepper_run_forced(st, C, amp, args.launches, mode="direct")
         torch.cuda.synchronize()
         print(f"ok: {args.launches} forced CH steps N={N} M={M}")
+        return
+    if args.kind == "ch_step":
+        # direct (ungraphed) no-flux Cahn-Hilliard steps with the workload's parameters
+        w = synth.WORKLOADS["cahn_hilliard"]
+        N, M = args.N, args.M
+        st = sb.sb_stepper_create("cahn_hilliard", "be", "noflux", N, w["gamma"], w["dt"])
+        C = synth.torch_uniform(w["seed"], N, M, -w["amp"], w["amp"], torch.float64, "cuda")
+        if args.step == "fp64":
+            sb.sb_stepper_run(st, C, args.launches, mode="direct")
+        else:
+            work = torch.empty(sb.sb_stepper_refined_workspace_bytes(st, M), dtype=torch.uint8, device="cuda")
+            sb.sb_stepper_run_refined(st, C, args.launches, work, n_refine=2, mode="direct")
+        torch.cuda.synchronize()
+        print(f"ok: {args.launches} {args.step} CH steps N={N} M={M}")
         return
     if args.kind == "tri":
         fac = sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", args.N, 0.5))
