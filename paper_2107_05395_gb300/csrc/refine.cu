@@ -236,6 +236,208 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, TB, double> a) {
                                      a.work[g], tile);
 }
 
+// ------------------------------------------------ staged refinement pass
+//
+// The same correction pass with its row streams staged through shared memory by
+// cp.async: kStageRows rows of each stream are in flight per thread without
+// holding them in registers.  The register-prefetched form above keeps 4 to 8 rows
+// in flight per warp, and the fused solve was bound by the latency of those loads
+// (more warps with fewer rows each, or fewer with more, ran no faster).  Each lane
+// copies, and later reads, only its own system's values, so the thread's own
+// cp.async.wait_group is the only ordering needed; a slot is refilled after the row
+// read from it has been computed and its result stored.
+constexpr int kStageRows = 16;
+constexpr int kStageBatch = 4;  // rows taken per wait in the correction passes
+constexpr int kStagedThreads = 512;  // one CTA per SM: its registers fill the SM
+
+__device__ __forceinline__ uint32_t shared_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8, "per-lane copies of 4 or 8 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(shared_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// Shared-memory bytes of the staging ring of a block of `threads` threads: D slots
+// of an FP64 value and of a right-hand-side value per thread.
+template <typename TB>
+constexpr size_t stage_ring_bytes(int threads) {
+  return (size_t)kStageRows * threads * (sizeof(double) + sizeof(TB));
+}
+
+template <int P, bool DFRES, typename TB>
+__device__ __forceinline__ void refine_tile_staged(const float* fw, const float* bw,
+                                                   const typename Residual<DFRES>::AC* arow, int N,
+                                                   int64_t M, int64_t ld, const TB* b, double* x,
+                                                   float* g, int64_t tile, unsigned char* ring) {
+  using RS = Residual<DFRES>;
+  using X = typename RS::X;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  constexpr int D = kStageRows;
+  constexpr int K = kStageBatch;
+  static_assert((D & (D - 1)) == 0 && D % K == 0, "the ring length is a power of two and a multiple of K");
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const TB* bp = b + m;
+  double* xp = x + m;
+  float* gp = g + m;
+  const int T = blockDim.x;
+  // slot s of this thread: rx[s * T] (FP64) and rb[s * T] (a right-hand-side value,
+  // or the FP32 intermediate in the backward sweep)
+  double* rx = reinterpret_cast<double*>(ring) + threadIdx.x;
+  TB* rb = reinterpret_cast<TB*>(ring + (size_t)D * T * sizeof(double)) + threadIdx.x;
+  __threadfence_block();  // this thread's stores of x (earlier passes) before the copies read them
+
+  // ---- forward: iteration i takes x_{i+P} (the window's new row) and b_i
+  X xw[NB];  // x_{i-P} .. x_{i+P}
+#pragma unroll
+  for (int k = 0; k < NB; ++k) xw[k] = RS::in(0.0);
+  auto push = [&](double v) {
+#pragma unroll
+    for (int k = 0; k < NB - 1; ++k) xw[k] = xw[k + 1];
+    xw[NB - 1] = RS::in(v);
+  };
+#pragma unroll
+  for (int k = 0; k < P; ++k) push(k < N ? xp[(int64_t)k * ld] : 0.0);  // rows 0 .. P-1 enter first
+  auto issue_f = [&](int k) {
+    const int s = (k & (D - 1)) * T;
+    if (k + P < N) cp_async<8>(rx + s, xp + (int64_t)(k + P) * ld);
+    if (k < N) cp_async<sizeof(TB)>(rb + s, bp + (int64_t)k * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_f(k);
+  // rows in batches of K: the K residuals are independent of each other and of the
+  // FP32 recurrence, so their FP64 FMA chains overlap; then the K sweep steps
+  float u1 = 0.f, u2 = 0.f;
+  for (int i0 = 0; i0 < N; i0 += K) {
+    cp_wait<D - K>();  // the groups of rows i0 .. i0+K-1 are complete
+    float r[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int i = i0 + j;
+      const int s = (i & (D - 1)) * T;
+      push(i + P < N ? rx[s] : 0.0);
+      r[j] = i < N ? RS::template eval<NB>(arow + NB * i, xw, rb[s]) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int i = i0 + j;
+      if (i < N) {
+        const float u = NativeArith<float>::step<P, false>(fw + W * i, r[j], u1, u2);
+        gp[(int64_t)i * ld] = u;
+        u2 = u1;
+        u1 = u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_f(i0 + D + j);  // refills the K slots used above
+  }
+  cp_wait<0>();           // every group left is empty (rows past N)
+  __threadfence_block();  // the stores of g before the copies that read them back
+
+  // ---- backward: iteration k takes row i = N-1-k of g and of x; x_i += d_i
+  auto issue_b = [&](int k) {
+    const int i = N - 1 - k;
+    const int s = (k & (D - 1)) * T;
+    if (i >= 0) {
+      cp_async<4>(reinterpret_cast<float*>(rb + s), gp + (int64_t)i * ld);
+      cp_async<8>(rx + s, xp + (int64_t)i * ld);
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_b(k);
+  float d1 = 0.f, d2 = 0.f;
+  for (int k0 = 0; k0 < N; k0 += K) {
+    cp_wait<D - K>();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int k = k0 + j;
+      const int i = N - 1 - k;
+      const int s = (k & (D - 1)) * T;
+      if (i >= 0) {
+        const float d =
+            NativeArith<float>::step<P, true>(bw + W * i, *reinterpret_cast<const float*>(rb + s), d1, d2);
+        st_stream(xp + (int64_t)i * ld, rx[s] + widen_f32(d));
+        d2 = d1;
+        d1 = d;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_b(k0 + D + j);
+  }
+  cp_wait<0>();
+}
+
+// The FP32 pass x_0 = sweep32(b) with the same staging: the forward sweep streams b
+// and stores its FP32 intermediate densely in the workspace g (4 bytes per element;
+// the unstaged pass keeps it in x's 8-byte slots), the backward sweep streams it
+// back and stores x_0 widened to FP64.  The arithmetic is that of
+// sweep_tile<NativeArith<float>, P, false, true>.
+template <int P, typename TB>
+__device__ __forceinline__ void sweep32_tile_staged(const float* fw, const float* bw, int N, int64_t M,
+                                                    int64_t ld, const TB* b, double* x, float* g,
+                                                    int64_t tile, unsigned char* ring) {
+  using A = NativeArith<float>;
+  constexpr int W = P + 1;
+  constexpr int D = kStageRows;
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const TB* bp = b + m;
+  double* xp = x + m;
+  float* gp = g + m;
+  const int T = blockDim.x;
+  TB* rb = reinterpret_cast<TB*>(ring + (size_t)D * T * sizeof(double)) + threadIdx.x;
+  __threadfence_block();  // this thread's earlier stores of g before the copies below
+
+  auto issue_f = [&](int k) {
+    if (k < N) cp_async<sizeof(TB)>(rb + (k & (D - 1)) * T, bp + (int64_t)k * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_f(k);
+  float u1 = 0.f, u2 = 0.f;
+  for (int i = 0; i < N; ++i) {
+    cp_wait<D - 1>();
+    const float u = A::step<P, false>(fw + W * i, Conv<A, TB>::in(rb[(i & (D - 1)) * T]), u1, u2);
+    gp[(int64_t)i * ld] = u;
+    u2 = u1;
+    u1 = u;
+    issue_f(i + D);
+  }
+  cp_wait<0>();
+  __threadfence_block();  // the stores of g before the copies that read them back
+
+  auto issue_b = [&](int k) {
+    const int i = N - 1 - k;
+    if (i >= 0) cp_async<4>(reinterpret_cast<float*>(rb + (k & (D - 1)) * T), gp + (int64_t)i * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_b(k);
+  float x1 = 0.f, x2 = 0.f;
+  for (int k = 0; k < N; ++k) {
+    cp_wait<D - 1>();
+    const int i = N - 1 - k;
+    const float xi = A::step<P, true>(bw + W * i, *reinterpret_cast<const float*>(rb + (k & (D - 1)) * T), x1, x2);
+    st_stream(xp + (int64_t)i * ld, widen_f32(xi));
+    x2 = x1;
+    x1 = xi;
+    issue_b(k + D);
+  }
+  cp_wait<0>();
+}
+
 // All passes in one launch: each warp takes a tile and runs the FP32 pass (x_0 into
 // x) and then the n_refine correction passes on it, before its next tile.  Tiles are
 // independent, so no pass waits for another tile; warps drift into different passes,
@@ -244,9 +446,13 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, TB, double> a) {
 // 128 registers, so two 256-thread CTAs share an SM.
 constexpr int kFusedRows = 4;
 
-template <int P, bool DFRES, typename TB>
-__global__ void __launch_bounds__(256, 2)
-grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a, int n_refine) {
+// STAGED: the correction passes stream their rows through a shared-memory ring
+// (refine_tile_staged; 512 threads, one CTA per SM) placed after the coefficients at
+// ring_off bytes; otherwise the register-prefetched passes (256 threads, two CTAs).
+template <int P, bool DFRES, typename TB, bool STAGED>
+__global__ void __launch_bounds__(STAGED ? kStagedThreads : 256, STAGED ? 1 : 2)
+grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a, int n_refine,
+                             unsigned ring_off) {
   using AC = typename Residual<DFRES>::AC;
   constexpr int W = P + 1;
   constexpr int NB = 2 * P + 1;
@@ -262,11 +468,20 @@ grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a
   const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
   for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
        tile < a.ntiles[g]; tile += (int64_t)ctas * nw) {
-    sweep_tile<NativeArith<float>, P, false, true, TB, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[g], a.ld[g],
-                                                                        a.rhs[g], a.x[g], tile);
-    for (int k = 0; k < n_refine; ++k)
-      refine_tile<P, DFRES, kFusedRows, TB>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g], a.work[g],
-                                       tile);
+    if constexpr (STAGED)
+      sweep32_tile_staged<P, TB>(cs, cs + W * N, N, a.M[g], a.ld[g], a.rhs[g], a.x[g], a.work[g], tile,
+                                 smem_raw + ring_off);
+    else
+      sweep_tile<NativeArith<float>, P, false, true, TB, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[g],
+                                                                              a.ld[g], a.rhs[g], a.x[g], tile);
+    for (int k = 0; k < n_refine; ++k) {
+      if constexpr (STAGED)
+        refine_tile_staged<P, DFRES, TB>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g], a.work[g],
+                                         tile, smem_raw + ring_off);
+      else
+        refine_tile<P, DFRES, kFusedRows, TB>(cs, cs + W * N, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g],
+                                              a.work[g], tile);
+    }
   }
 }
 
@@ -365,7 +580,7 @@ refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, dou
 constexpr int kThreads = 256;
 
 template <typename K>
-int resident_ctas(K kernel, int device, size_t smem, int* total) {
+int resident_ctas(K kernel, int device, size_t smem, int* total, int threads = kThreads) {
   static std::mutex mu;
   static std::map<std::pair<const void*, size_t>, int> cache;
   int nb = 0;
@@ -377,7 +592,7 @@ int resident_ctas(K kernel, int device, size_t smem, int* total) {
       nb = it->second;
     } else {
       SB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-      SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem));
+      SB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem));
       cache[key] = nb;
     }
   }
@@ -455,11 +670,16 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
                               (size_t)2 * (P + 1) * f[g]->N * sizeof(float));
   }
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
-  auto k = grouped_refined_solve_kernel<P, DFRES, TB>;
+  // the staged passes when their ring fits beside the coefficients
+  const size_t ring_off = (smem + 15) / 16 * 16;
+  const bool staged = n_refine > 0 && ring_off + stage_ring_bytes<TB>(kStagedThreads) <= (size_t)kMaxDynSmem;
+  auto k = staged ? grouped_refined_solve_kernel<P, DFRES, TB, true> : grouped_refined_solve_kernel<P, DFRES, TB, false>;
+  const int threads = staged ? kStagedThreads : kThreads;
+  if (staged) smem = ring_off + stage_ring_bytes<TB>(kStagedThreads);
   int total = 0;
-  SB_TRY(resident_ctas(k, f[0]->device, smem, &total));
+  SB_TRY(resident_ctas(k, f[0]->device, smem, &total, threads));
   const int grid = plan(a, f, total);
-  k<<<grid, kThreads, smem, stream>>>(a, n_refine);
+  k<<<grid, threads, smem, stream>>>(a, n_refine, (unsigned)ring_off);
   return cuda_check(cudaGetLastError(), "refined solve launch");
 }
 

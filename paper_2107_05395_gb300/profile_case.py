@@ -3,6 +3,7 @@
     python -m paper_2107_05395_gb300.profile_case --kind penta --N 1024 --M 32768 --launches 3
     python -m paper_2107_05395_gb300.profile_case --kind forced_ch --N 512 --M 65536 --launches 3
     python -m paper_2107_05395_gb300.profile_case --kind ch_step --step refined --N 256 --M 65536 --launches 3
+    python -m paper_2107_05395_gb300.profile_case --kind groups --total 131072 --launches 3
 
 Everything goes through the C ABI; inputs are seeded N(0, 1) drawn on the device.
 The default case keeps the inputs above the L2 size (so DRAM counters mean
@@ -19,7 +20,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["tri", "penta", "forced_ch", "ch_step"], default="penta")
+    ap.add_argument("--kind", choices=["tri", "penta", "forced_ch", "ch_step", "groups"], default="penta")
     ap.add_argument("--step", choices=["fp64", "refined"], default="fp64",
                     help="ch_step: the fused FP64 step or the FP32 + 2 refinements step")
     ap.add_argument("--N", type=int, default=1024)
@@ -28,6 +29,10 @@ def main():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--arith", choices=["native", "df32"], default="native")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--total", type=int, default=131072,
+                    help="groups: right-hand sides over the three tridiagonal groups (N = 128/512/2048, 4:2:1)")
+    ap.add_argument("--n-refine", type=int, default=2, help="groups: correction passes")
+    ap.add_argument("--residual", choices=["native", "df32"], default="native", help="groups: residual arithmetic")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape first")
     ap.add_argument("--shape", default=None, help="threads,ctas_per_sm,systems_per_thread[,algorithm]")
     args = ap.parse_args()
@@ -67,6 +72,24 @@ def main():
             sb.sb_stepper_run_refined(st, C, args.launches, work, n_refine=2, mode="direct")
         torch.cuda.synchronize()
         print(f"ok: {args.launches} {args.step} CH steps N={N} M={M}")
+        return
+    if args.kind == "groups":
+        # the multi-group mixed-precision workload at a chosen total batch: FP32
+        # right-hand sides U(-1, 1), FP64 solutions, one launch for every pass
+        w = synth.WORKLOADS["multigroup_fp32"]
+        Ms = synth.group_split(args.total, w["ratio"], w["N"])
+        facs, rhs, xs, work = [], [], [], []
+        for g, (N, r, M) in enumerate(zip(w["N"], w["r"], Ms)):
+            facs.append(sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", N, r)))
+            rhs.append(synth.torch_uniform(w["seed"] + g, N, M, -1.0, 1.0, torch.float32, "cuda"))
+            xs.append(torch.empty((N, M), dtype=torch.float64, device="cuda"))
+            work.append(torch.empty((N, M), dtype=torch.float32, device="cuda"))
+        for _ in range(args.launches):
+            sb.sb_solve_batched_groups(facs, rhs, xs, work=work, n_refine=args.n_refine,
+                                       residual_arith=args.residual)
+        torch.cuda.synchronize()
+        print(f"ok: {args.launches} grouped solves, {args.n_refine} refinements ({args.residual} residual), "
+              f"batches {list(Ms)}")
         return
     if args.kind == "tri":
         fac = sb.sb_factor_shared_tri(*sb.sb_build_matrix("diffusion", args.N, 0.5))
