@@ -210,19 +210,30 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
  *                        boundary system solved by cyclic reduction when every CTA
  *                        has one tile (latency-bound batches), else by block
  *                        Thomas; same fallback.
+ *   SB_ALGO_STAGED       the sequential sweeps with both row streams (the rhs in the
+ *                        forward sweep, the intermediate in the backward sweep) staged
+ *                        through a ring of 8 rows per thread in shared memory by
+ *                        cp.async, so the rows in flight take no registers and a CTA
+ *                        can run up to 1024 threads (512 in double-float
+ *                        arithmetic).  Same arithmetic and results as
+ *                        SB_ALGO_SEQUENTIAL; applies to non-periodic factors whose
+ *                        coefficients and ring fit in one CTA's shared memory, else
+ *                        the sequential sweeps run with their default shape.
  */
-typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1 } sb_algo;
+typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1, SB_ALGO_STAGED = 2 } sb_algo;
 
 /*
  * Launch shape of a batched solve.
  *   threads             threads per CTA: a multiple of 32 in [32, 512] for
- *                       SB_ALGO_SEQUENTIAL; 256 (16 chunks, two systems per thread),
+ *                       SB_ALGO_SEQUENTIAL, in [32, 1024] for SB_ALGO_STAGED (at most
+ *                       512 in double-float arithmetic); 256 (16 chunks, two systems per thread),
  *                       512 (16 chunks) or 1024 (32 chunks) for SB_ALGO_PARTITIONED
  *                       with FP32 rhs, 128 for its FP64 form.
  *   ctas_per_sm         cap on resident CTAs per SM (0 = as many as fit; 0 or 1 for
  *                       SB_ALGO_PARTITIONED, which fits one).
  *   systems_per_thread  1 or 2 for SB_ALGO_SEQUENTIAL (each thread interleaves that
- *                       many independent recurrences); 1 for SB_ALGO_PARTITIONED.
+ *                       many independent recurrences); 1 for SB_ALGO_PARTITIONED and
+ *                       SB_ALGO_STAGED.
  *   algorithm           an sb_algo.
  */
 typedef struct {

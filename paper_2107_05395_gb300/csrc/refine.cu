@@ -250,22 +250,6 @@ constexpr int kStageRows = 16;
 constexpr int kStageBatch = 4;  // rows taken per wait in the correction passes
 constexpr int kStagedThreads = 512;  // one CTA per SM: its registers fill the SM
 
-__device__ __forceinline__ uint32_t shared_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-template <int B>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  static_assert(B == 4 || B == 8, "per-lane copies of 4 or 8 bytes");
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(shared_addr(dst)),
-               "l"(__cvta_generic_to_global(src)), "n"(B)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
-}
-
 // Shared-memory bytes of the staging ring of a block of `threads` threads: D slots
 // of an FP64 value and of a right-hand-side value per thread.
 template <typename TB>

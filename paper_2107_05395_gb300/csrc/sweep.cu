@@ -61,6 +61,35 @@ sweep_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t l
                                                          cy, alpha, beta);
 }
 
+// Staged single-factor kernel (SB_ALGO_STAGED): the coefficients as above, then a
+// ring of kStagedRows slots per thread for the rows in flight (sweep_tile_staged),
+// so that up to 1024 threads per CTA fit in the registers (512 in double-float
+// arithmetic, whose values take two registers).
+constexpr int kStagedRows = 8;
+constexpr int kStagedBatch = 4;
+
+template <class A>
+__host__ __device__ constexpr int staged_max_threads() {
+  return std::is_same_v<A, DFArith> ? 512 : 1024;
+}
+
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO>
+__global__ void __launch_bounds__(staged_max_threads<A>())
+sweep_staged_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, int64_t ld, const TI* rhs,
+                    TO* x, int64_t ntiles, unsigned ring_off) {
+  using C = typename A::C;
+  constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* cs = reinterpret_cast<C*>(smem_raw);
+  stage(cs, coef, 2 * W * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
+       tile += (int64_t)gridDim.x * nw)
+    sweep_tile_staged<A, P, F_ONE, B_ONE, TI, TO, kStagedRows, kStagedBatch>(cs, cs + W * N, N, M, ld, rhs, x,
+                                                                            tile, smem_raw + ring_off);
+}
+
 // The periodic correction data of a factor for an arithmetic policy: (w_i, -z_i)
 // rows of op `o` and the scalars alpha, beta as coefficients.
 template <class A>
@@ -133,9 +162,46 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   return cuda_check(cudaGetLastError(), "sweep kernel launch");
 }
 
+// The staged sweeps, or -1 (nothing launched) where they do not apply: periodic
+// factors, or coefficients and ring beyond one CTA's shared memory.
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int CYC>
+int launch_staged(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
+                  int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+  using C = typename A::C;
+  if constexpr (CYC != 0) {
+    return -1;
+  } else {
+    const int N = (int)f->N;
+    const int threads = shape.threads;
+    if (threads < 32 || threads > staged_max_threads<A>() || threads % 32 != 0)
+      return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, %d] for the staged sweeps",
+                  staged_max_threads<A>());
+    const size_t ring_off = ((size_t)2 * (P + 1) * N * sizeof(C) + 15) / 16 * 16;
+    const size_t smem =
+        ring_off + (size_t)kStagedRows * threads * staged_slot_bytes<TI, typename A::S>();
+    if (smem > (size_t)kMaxDynSmem) return -1;
+    auto k = sweep_staged_kernel<A, P, F_ONE, B_ONE, TI, TO>;
+    int nb = 0;
+    SB_TRY(kernel_occupancy(reinterpret_cast<const void*>(k), f->device, threads, smem, &nb));
+    if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
+    const int64_t ntiles = (M + 31) / 32;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
+    k<<<(unsigned)grid, threads, smem, stream>>>(coef, N, M, ld, static_cast<const TI*>(rhs),
+                                                static_cast<TO*>(x), ntiles, (unsigned)ring_off);
+    return cuda_check(cudaGetLastError(), "staged sweep kernel launch");
+  }
+}
+
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int CYC>
 int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
                int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
+  if (shape.algo == SB_ALGO_STAGED) {
+    const int rc = launch_staged<A, P, F_ONE, B_ONE, TI, TO, CYC>(f, coef, rhs, x, M, ld, shape, stream);
+    if (rc != -1) return rc;
+    // where the staged sweeps do not apply, the sequential ones with the default shape
+    const sb_arith arith = std::is_same_v<A, DFArith> ? SB_ARITH_DF32 : SB_ARITH_NATIVE;
+    return launch_spt<A, P, F_ONE, B_ONE, TI, TO, CYC>(f, coef, rhs, x, M, ld, default_shape(f, arith), stream, op);
+  }
   if (shape.spt == 2)
     return launch<A, P, F_ONE, B_ONE, TI, TO, 2, 4, CYC>(f, coef, rhs, x, M, ld, shape, stream, op);
   if (shape.spt != 1) return fail(SB_ERR_INVALID_ARG, "systems per thread must be 1 or 2");
@@ -220,7 +286,8 @@ int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype,
     return launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, default_shape(f, arith),
                         stream);
   }
-  if (shape.algo != SB_ALGO_SEQUENTIAL) return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape.algo);
+  if (shape.algo != SB_ALGO_SEQUENTIAL && shape.algo != SB_ALGO_STAGED)
+    return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape.algo);
   if (arith == SB_ARITH_NATIVE) {
     if (rhs_dtype == SB_F64 && x_dtype == SB_F64)
       return dispatch_pb<NativeArith<double>, double, double>(f, op, f->coef64, rhs, x, M, ld,

@@ -45,6 +45,24 @@ __device__ __forceinline__ void stage(C* dst, const C* __restrict__ src, int n) 
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+// Per-lane asynchronous copies global -> shared (cp.async, 4 or 8 bytes), their
+// commit groups, and the wait until at most K groups of this thread are pending.
+__device__ __forceinline__ uint32_t shared_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8, "per-lane copies of 4 or 8 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(shared_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
 // Solves the tile `tile` (32 * SPT consecutive systems) with coefficient rows
 // fw (forward) and bw (backward).  CYC = 1: the periodic tridiagonal matrix of
 // section 3.3: rows cy = (w_i, -z_i) and scalars alpha, beta give the
@@ -187,6 +205,95 @@ __device__ __forceinline__ void sweep_tile(const typename A::C* fw, const typena
       bwd(sb_, i0 - R);
     }
   } while (false);
+}
+
+// The same sweeps (plain matrices, one system per thread) with both row streams
+// staged through shared memory: a ring of D slots per thread (slot s of thread t at
+// ring + (s * blockDim.x + t) * E, E = max(sizeof(TI), sizeof(S))) holds the next D
+// rows of the right-hand side in the forward sweep and of the intermediate in the
+// backward sweep, so the rows in flight cost shared memory instead of registers and
+// a block can run more warps.  Each lane copies, and later reads, only its own
+// system's values, so the thread's own cp.async.wait_group is the only ordering; a
+// slot is refilled after the row read from it has been computed and stored.  Rows
+// are taken K per wait.  Same arithmetic as sweep_tile with SPT = 1, CYC = 0.
+template <typename TI, typename S>
+__host__ __device__ constexpr int staged_slot_bytes() {
+  return sizeof(TI) > sizeof(S) ? (int)sizeof(TI) : (int)sizeof(S);
+}
+
+template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int D, int K>
+__device__ __forceinline__ void sweep_tile_staged(const typename A::C* fw, const typename A::C* bw, int N,
+                                                  int64_t M, int64_t ld, const TI* rhs, TO* x, int64_t tile,
+                                                  unsigned char* ring) {
+  using V = typename A::V;
+  using S = typename A::S;
+  static_assert(sizeof(S) <= sizeof(TO), "intermediate must fit in an output element");
+  static_assert((D & (D - 1)) == 0 && D % K == 0, "the ring length is a power of two and a multiple of K");
+  constexpr int W = P + 1;
+  constexpr int E = staged_slot_bytes<TI, S>();
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const TI* r = rhs + m;
+  TO* y = x + m;
+  const int T = blockDim.x;
+  unsigned char* mine = ring + (size_t)threadIdx.x * E;
+  auto slot = [&](int k) { return mine + (size_t)(k & (D - 1)) * T * E; };
+  __threadfence_block();  // this thread's stores of the previous tile before the copies below
+
+  // ---- forward sweep: u_i from rhs_i, stored in place in x
+  auto issue_f = [&](int k) {
+    if (k < N) cp_async<sizeof(TI)>(slot(k), r + (int64_t)k * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_f(k);
+  V u1 = A::zero(), u2 = A::zero();
+  for (int i0 = 0; i0 < N; i0 += K) {
+    cp_wait<D - K>();  // the groups of rows i0 .. i0+K-1 are complete
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int i = i0 + j;
+      if (i < N) {
+        const V u = A::template step<P, F_ONE>(fw + W * i, Conv<A, TI>::in(*reinterpret_cast<const TI*>(slot(i))),
+                                               u1, u2);
+        *reinterpret_cast<S*>(y + (int64_t)i * ld) = A::to_store(u);
+        u2 = u1;
+        u1 = u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_f(i0 + D + j);
+  }
+  cp_wait<0>();           // every group left is empty (rows past N)
+  __threadfence_block();  // the stores of u before the copies that read them back
+
+  // ---- backward sweep: iteration k takes row i = N-1-k of u and writes x_i over it
+  auto issue_b = [&](int k) {
+    const int i = N - 1 - k;
+    if (i >= 0) cp_async<sizeof(S)>(slot(k), reinterpret_cast<const S*>(y + (int64_t)i * ld));
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue_b(k);
+  V x1 = A::zero(), x2 = A::zero();
+  for (int k0 = 0; k0 < N; k0 += K) {
+    cp_wait<D - K>();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int k = k0 + j;
+      const int i = N - 1 - k;
+      if (i >= 0) {
+        const V xi = A::template step<P, B_ONE>(bw + W * i, A::from_store(*reinterpret_cast<const S*>(slot(k))),
+                                                x1, x2);
+        st_stream(y + (int64_t)i * ld, Conv<A, TO>::out(xi));
+        x2 = x1;
+        x1 = xi;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_b(k0 + D + j);
+  }
+  cp_wait<0>();
 }
 
 }  // namespace sb
