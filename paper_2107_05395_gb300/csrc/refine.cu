@@ -249,6 +249,7 @@ grouped_refine_kernel(const __grid_constant__ Groups<float, TB, double> a) {
 constexpr int kStageRows = 16;
 constexpr int kStageBatch = 4;  // rows taken per wait in the correction passes
 constexpr int kStagedThreads = 512;  // one CTA per SM: its registers fill the SM
+constexpr bool kRefinedStepStaged = true;
 
 // Shared-memory bytes of the staging ring of a block of `threads` threads: D slots
 // of an FP64 value and of a right-hand-side value per thread.
@@ -530,10 +531,13 @@ __device__ __forceinline__ void rhs_tile(const double* rc, int N, int64_t M, int
 // state C through its right-hand side f (FP64, into the workspace), the FP32 solve
 // of f into C (in place: the tile's C is read completely first) and n_refine
 // correction passes with the FP64 f.  a.G == 1, a.rhs[0] == f, a.x[0] == C.
-template <int P, bool DFRES, int NB, bool HAS_E>
-__global__ void __launch_bounds__(256, 2)
+// STAGED: the FP32 pass and the correction passes stream their rows through the
+// shared-memory ring at ring_off (512 threads, one CTA per SM), as in the grouped
+// refined solve.
+template <int P, bool DFRES, int NB, bool HAS_E, bool STAGED>
+__global__ void __launch_bounds__(STAGED ? kStagedThreads : 256, STAGED ? 1 : 2)
 refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, double* f,
-                    const double* __restrict__ rcoef, int n_refine) {
+                    const double* __restrict__ rcoef, int n_refine, unsigned ring_off) {
   using AC = typename Residual<DFRES>::AC;
   constexpr int W = P + 1;
   constexpr int NBA = 2 * P + 1;
@@ -551,11 +555,19 @@ refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, dou
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < a.ntiles[0];
        tile += (int64_t)gridDim.x * nw) {
     rhs_tile<NB, HAS_E, kFusedRows>(rs, N, a.M[0], a.ld[0], a.x[0], f, tile);
-    sweep_tile<NativeArith<float>, P, false, true, double, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[0],
-                                                                                a.ld[0], f, a.x[0], tile);
-    for (int k = 0; k < n_refine; ++k)
-      refine_tile<P, DFRES, kFusedRows, double>(cs, cs + W * N, as, N, a.M[0], a.ld[0], f, a.x[0], a.work[0],
-                                                tile);
+    if constexpr (STAGED) {
+      sweep32_tile_staged<P, double>(cs, cs + W * N, N, a.M[0], a.ld[0], f, a.x[0], a.work[0], tile,
+                                     smem_raw + ring_off);
+      for (int k = 0; k < n_refine; ++k)
+        refine_tile_staged<P, DFRES, double>(cs, cs + W * N, as, N, a.M[0], a.ld[0], f, a.x[0], a.work[0], tile,
+                                             smem_raw + ring_off);
+    } else {
+      sweep_tile<NativeArith<float>, P, false, true, double, double, 1, kFusedRows>(cs, cs + W * N, N, a.M[0],
+                                                                                  a.ld[0], f, a.x[0], tile);
+      for (int k = 0; k < n_refine; ++k)
+        refine_tile<P, DFRES, kFusedRows, double>(cs, cs + W * N, as, N, a.M[0], a.ld[0], f, a.x[0], a.work[0],
+                                                  tile);
+    }
   }
 }
 
@@ -687,13 +699,19 @@ int launch_refined_step(const sb_factor* f, const double* rcoef, double* state, 
                       (size_t)RW * f->N * sizeof(double);
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "N=%lld: the step's coefficients exceed shared memory",
                                      (long long)f->N);
-  auto k = refined_step_kernel<P, DFRES, NB, HAS_E>;
+  // the staged passes when their ring fits beside the coefficients
+  const size_t ring_off = (smem + 15) / 16 * 16;
+  const bool staged = kRefinedStepStaged && n_refine > 0 &&
+                      ring_off + stage_ring_bytes<double>(kStagedThreads) <= (size_t)kMaxDynSmem;
+  auto k = staged ? refined_step_kernel<P, DFRES, NB, HAS_E, true> : refined_step_kernel<P, DFRES, NB, HAS_E, false>;
+  const int threads = staged ? kStagedThreads : kThreads;
+  const size_t smem_all = staged ? ring_off + stage_ring_bytes<double>(kStagedThreads) : smem;
   int total = 0;
-  SB_TRY(resident_ctas(k, f->device, smem, &total));
+  SB_TRY(resident_ctas(k, f->device, smem_all, &total, threads));
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ntiles[0], total));
   a.cta_begin[0] = 0;
   a.cta_begin[1] = (int)grid;
-  k<<<(unsigned)grid, kThreads, smem, stream>>>(a, fbuf, rcoef, n_refine);
+  k<<<(unsigned)grid, threads, smem_all, stream>>>(a, fbuf, rcoef, n_refine, (unsigned)ring_off);
   return cuda_check(cudaGetLastError(), "refined step launch");
 }
 
