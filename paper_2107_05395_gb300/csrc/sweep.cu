@@ -162,14 +162,15 @@ int launch(const sb_factor* f, const typename A::C* coef, const void* rhs, void*
   return cuda_check(cudaGetLastError(), "sweep kernel launch");
 }
 
-// The staged sweeps, or -1 (nothing launched) where they do not apply: periodic
-// factors, or coefficients and ring beyond one CTA's shared memory.
+// The staged sweeps; *applied = false (nothing launched, SB_OK) where they do not
+// apply: periodic factors, or coefficients and ring beyond one CTA's shared memory.
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int CYC>
 int launch_staged(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
-                  int64_t ld, const SweepShape& shape, cudaStream_t stream) {
+                  int64_t ld, const SweepShape& shape, cudaStream_t stream, bool* applied) {
   using C = typename A::C;
+  *applied = false;
   if constexpr (CYC != 0) {
-    return -1;
+    return SB_OK;
   } else {
     const int N = (int)f->N;
     const int threads = shape.threads;
@@ -179,7 +180,8 @@ int launch_staged(const sb_factor* f, const typename A::C* coef, const void* rhs
     const size_t ring_off = ((size_t)2 * (P + 1) * N * sizeof(C) + 15) / 16 * 16;
     const size_t smem =
         ring_off + (size_t)kStagedRows * threads * staged_slot_bytes<TI, typename A::S>();
-    if (smem > (size_t)kMaxDynSmem) return -1;
+    if (smem > (size_t)kMaxDynSmem) return SB_OK;
+    *applied = true;
     auto k = sweep_staged_kernel<A, P, F_ONE, B_ONE, TI, TO>;
     int nb = 0;
     SB_TRY(kernel_occupancy(reinterpret_cast<const void*>(k), f->device, threads, smem, &nb));
@@ -196,8 +198,9 @@ template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int 
 int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
                int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
   if (shape.algo == SB_ALGO_STAGED) {
-    const int rc = launch_staged<A, P, F_ONE, B_ONE, TI, TO, CYC>(f, coef, rhs, x, M, ld, shape, stream);
-    if (rc != -1) return rc;
+    bool applied = false;
+    const int rc = launch_staged<A, P, F_ONE, B_ONE, TI, TO, CYC>(f, coef, rhs, x, M, ld, shape, stream, &applied);
+    if (rc != SB_OK || applied) return rc;
     // where the staged sweeps do not apply, the sequential ones with the default shape
     const sb_arith arith = std::is_same_v<A, DFArith> ? SB_ARITH_DF32 : SB_ARITH_NATIVE;
     return launch_spt<A, P, F_ONE, B_ONE, TI, TO, CYC>(f, coef, rhs, x, M, ld, default_shape(f, arith), stream, op);
