@@ -883,6 +883,9 @@ def run_ours(args):
     def headline_kernel(policy, what):
         # the kernel the autotuner's shape for this arithmetic launches
         shp = shapes[arith][0]
+        if shp[3] == sb.SB_ALGO_TWO_ENDED:
+            return (f"sweep_two_ended_kernel<P=2> ({what}; each system eliminated from both ends, "
+                    f"16 systems per warp, {shp[0]} threads)")
         if shp[3] == sb.SB_ALGO_STAGED:
             return f"sweep_staged_kernel<{policy},P=2> ({what}; rows staged through shared memory, {shp[0]} threads)"
         return f"sweep_kernel<{policy},P=2> ({what}; {shp[0]} threads, {shp[2]} system(s) per thread)"

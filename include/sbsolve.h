@@ -219,21 +219,38 @@ int sb_solve_batched_ex(const sb_factor* f, int transpose, const void* rhs, sb_d
  *                        SB_ALGO_SEQUENTIAL; applies to non-periodic factors whose
  *                        coefficients and ring fit in one CTA's shared memory, else
  *                        the sequential sweeps run with their default shape.
+ *   SB_ALGO_TWO_ENDED    this library's own: every system is eliminated from its
+ *                        first row downwards and from its last row upwards at the
+ *                        same time (LU of the top half and of the reversed bottom
+ *                        half, computed once in FP64 with the factorisation), the two
+ *                        halves meet in a 2P x 2P system whose inverse is precomputed,
+ *                        and the back substitution runs outwards from it: two
+ *                        independent recurrences per thread and the same FP64
+ *                        operations per element, exact up to rounding.  Rows staged
+ *                        as in SB_ALGO_STAGED.  Applies to FP64 rhs and x in native
+ *                        arithmetic, non-periodic factors, N >= 4 (tridiagonal) or
+ *                        N >= 8 (pentadiagonal); elsewhere the sequential sweeps run
+ *                        with their default shape.
  */
-typedef enum { SB_ALGO_SEQUENTIAL = 0, SB_ALGO_PARTITIONED = 1, SB_ALGO_STAGED = 2 } sb_algo;
+typedef enum {
+  SB_ALGO_SEQUENTIAL = 0,
+  SB_ALGO_PARTITIONED = 1,
+  SB_ALGO_STAGED = 2,
+  SB_ALGO_TWO_ENDED = 3
+} sb_algo;
 
 /*
  * Launch shape of a batched solve.
  *   threads             threads per CTA: a multiple of 32 in [32, 512] for
  *                       SB_ALGO_SEQUENTIAL, in [32, 1024] for SB_ALGO_STAGED (at most
- *                       512 in double-float arithmetic); 256 (16 chunks, two systems per thread),
+ *                       512 in double-float arithmetic) and SB_ALGO_TWO_ENDED; 256
+ *                       (16 chunks, two systems per thread),
  *                       512 (16 chunks) or 1024 (32 chunks) for SB_ALGO_PARTITIONED
  *                       with FP32 rhs, 128 for its FP64 form.
  *   ctas_per_sm         cap on resident CTAs per SM (0 = as many as fit; 0 or 1 for
  *                       SB_ALGO_PARTITIONED, which fits one).
  *   systems_per_thread  1 or 2 for SB_ALGO_SEQUENTIAL (each thread interleaves that
- *                       many independent recurrences); 1 for SB_ALGO_PARTITIONED and
- *                       SB_ALGO_STAGED.
+ *                       many independent recurrences); 1 for the other algorithms.
  *   algorithm           an sb_algo.
  */
 typedef struct {

@@ -18,7 +18,7 @@ from ._lib import (  # noqa: F401
     sb_factor_info,
     sb_factor_shared_penta, sb_factor_shared_tri, sb_factor_shared_tri_periodic, sb_factor_shared_penta_periodic, sb_last_error, sb_solve_batched,
     sb_solve_batched_adjoint, sb_solve_batched_ex, sb_version, SB_ARITH_NATIVE, SB_ARITH_DF32,
-    Shape, SB_ALGO_SEQUENTIAL, SB_ALGO_PARTITIONED, SB_ALGO_STAGED, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run, sb_stepper_run_coarsening, sb_stepper_set_forcing, sb_stepper_run_forced, sb_stepper_refined_workspace_bytes, sb_stepper_run_refined,
+    Shape, SB_ALGO_SEQUENTIAL, SB_ALGO_PARTITIONED, SB_ALGO_STAGED, SB_ALGO_TWO_ENDED, sb_autotune, sb_shape_get, sb_shape_set, Stepper, sb_stepper_create, sb_stepper_run, sb_stepper_run_coarsening, sb_stepper_set_forcing, sb_stepper_run_forced, sb_stepper_refined_workspace_bytes, sb_stepper_run_refined,
     sb_refine_workspace_bytes, sb_solve_batched_refined, sb_solve_batched_groups,
     sb_solve_batched_refined_noalloc, sb_rollout_workspace_bytes, sb_rollout_forward,
     sb_rollout_backward, sb_host_workspace_bytes, sb_solve_batched_host, sb_device_timeouts, sb_measure_rates,

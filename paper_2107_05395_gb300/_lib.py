@@ -293,11 +293,12 @@ def sb_solve_batched_ex(f: Factor, rhs, x, transpose=False, arith="native", M=No
 SB_ALGO_SEQUENTIAL = 0
 SB_ALGO_PARTITIONED = 1
 SB_ALGO_STAGED = 2
+SB_ALGO_TWO_ENDED = 3
 
 
 class Shape(ctypes.Structure):
     """sb_shape: threads per CTA, resident CTAs per SM (0 = max), systems per thread,
-    algorithm (SB_ALGO_SEQUENTIAL, SB_ALGO_PARTITIONED or SB_ALGO_STAGED)."""
+    algorithm (SB_ALGO_SEQUENTIAL, SB_ALGO_PARTITIONED, SB_ALGO_STAGED or SB_ALGO_TWO_ENDED)."""
     _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("systems_per_thread", ctypes.c_int), ("algorithm", ctypes.c_int)]
 

@@ -11,6 +11,7 @@
 
 #include "partition.h"
 #include "sb_internal.h"
+#include "two_ended.h"
 
 namespace sb {
 
@@ -299,6 +300,23 @@ static int upload_factor(sb_factor* f) {
       }
     }
   }
+  // FP64 images of the two-ended sweeps of A and A^T
+  if (!f->periodic && N >= two_ended_min_n(f->P)) {
+    for (int o = 0; o < 2; ++o) {
+      std::vector<double> dt;
+      const double* d = f->h_diag.data();
+      if (o == 1) {
+        dt = transpose_diagonals(f->P, (int)N, d);
+        d = dt.data();
+      }
+      TwoEnded t;
+      if (!build_two_ended(f->P, (int)N, d, t)) continue;
+      const std::vector<double> img = two_ended_image(t);
+      SB_CUDA(cudaMalloc(&f->two_img[o], img.size() * sizeof(double)));
+      SB_CUDA(cudaMemcpy(f->two_img[o], img.data(), img.size() * sizeof(double), cudaMemcpyHostToDevice));
+      f->two_s = t.s;
+    }
+  }
   return SB_OK;
 }
 
@@ -317,6 +335,8 @@ static void free_factor(sb_factor* f) {
       for (float* p : per_op)
         if (p) cudaFree(p);
     for (double* p : f->part64_img)
+      if (p) cudaFree(p);
+    for (double* p : f->two_img)
       if (p) cudaFree(p);
   }
   delete f;

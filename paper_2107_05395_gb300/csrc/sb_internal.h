@@ -121,6 +121,11 @@ struct sb_factor {
   // A^T: 16 chunks of part64_L rows; null where it does not apply
   double* part64_img[2] = {nullptr, nullptr};
   int part64_L = 0;
+  // FP64 images of the two-ended sweeps (two_ended.h) of A and A^T: N forward rows,
+  // N backward rows, the (2P)^2 interface inverse; split row two_s; null where they
+  // do not apply (periodic factors, N < 4P, a zero pivot or a singular interface)
+  double* two_img[2] = {nullptr, nullptr};
+  int two_s = 0;
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64 (of A' for a periodic factor)

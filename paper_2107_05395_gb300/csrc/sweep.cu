@@ -90,6 +90,143 @@ sweep_staged_kernel(const typename A::C* __restrict__ coef, int N, int64_t M, in
                                                                             tile, smem_raw + ring_off);
 }
 
+// Two-ended kernel (SB_ALGO_TWO_ENDED; FP64 rhs and x, native arithmetic): every
+// system is eliminated from both ends at once (two_ended.h).  A warp takes 16
+// systems: lane l < 16 runs the top half of system l (rows 0 .. s-1 down, then back
+// up from the interface) and lane l + 16 its bottom half (rows N-1 .. s up, then back
+// down), so a batch gives twice as many warps, each with all 32 lanes busy; with
+// 65536 systems that is 6.7 warps per scheduler instead of 3.4, and the FP64 pipe
+// of the scheduler with the most warps no longer sets the time alone.  The two
+// halves of a system meet in the 2P x 2P interface system through one warp shuffle.
+// Each lane's rows go through a ring of kTwoRows slots in shared memory, as in the
+// staged sweeps.  Image in shared memory: fw (W N) | bw (W N) | the (2P)^2 interface
+// inverse.
+constexpr int kTwoRows = 8;
+constexpr int kTwoBatch = 4;
+
+template <int P>
+__device__ __forceinline__ void two_ended_tile(const double* fw, const double* bw, const double* minv, int N,
+                                               int s, int64_t M, int64_t ld, const double* rhs, double* x,
+                                               int64_t tile, unsigned char* ring) {
+  using A = NativeArith<double>;
+  constexpr int W = P + 1;
+  constexpr int D = kTwoRows;
+  constexpr int K = kTwoBatch;
+  constexpr int NZ = 2 * P;
+  static_assert((D & (D - 1)) == 0 && D % K == 0, "the ring length is a power of two and a multiple of K");
+  const int lane = threadIdx.x & 31;
+  const bool top = lane < 16;
+  const int64_t m = tile * 16 + (lane & 15);
+  // lanes l and l + 16 hold the same system, so both are in the mask or neither
+  const unsigned mask = __ballot_sync(0xffffffffu, m < M);
+  if (m >= M) return;
+  const double* r = rhs + m;
+  double* y = x + m;
+  const int T = blockDim.x;
+  double* rs = reinterpret_cast<double*>(ring) + threadIdx.x;  // slot k at rs[k * T]
+  __threadfence_block();  // this thread's stores of the previous tile before the copies below
+
+  // ---- forward: step t is row t (top) or row N-1-t (bottom); u in place in x
+  const int nf = top ? s : N - s;
+  const int TF = s > N - s ? s : N - s;
+  auto issue_f = [&](int t) {
+    if (t < nf) cp_async<8>(rs + (t & (D - 1)) * T, r + (int64_t)(top ? t : N - 1 - t) * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int t = 0; t < D; ++t) issue_f(t);
+  double v1 = 0.0, v2 = 0.0;
+  for (int t0 = 0; t0 < TF; t0 += K) {
+    cp_wait<D - K>();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int t = t0 + j;
+      if (t < nf) {
+        const int i = top ? t : N - 1 - t;
+        const double u = A::step<P, false>(fw + W * i, rs[(t & (D - 1)) * T], v1, v2);
+        y[(int64_t)i * ld] = u;
+        v2 = v1;
+        v1 = u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_f(t0 + D + j);
+  }
+  cp_wait<0>();
+  __threadfence_block();  // the stores of u before the copies that read them back
+
+  // ---- interface: z = (x_{s-P} .. x_{s+P-1}) = Minv (u_{s-P} .. u_{s+P-1}); the top
+  // lane ends at u_{s-1} (v1), u_{s-2} (v2), the bottom lane at u_s (v1), u_{s+1} (v2)
+  const double o1 = __shfl_xor_sync(mask, v1, 16);
+  const double o2 = __shfl_xor_sync(mask, v2, 16);
+  double uz[NZ];
+  if constexpr (P == 2) {
+    uz[0] = top ? v2 : o2;
+    uz[1] = top ? v1 : o1;
+    uz[2] = top ? o1 : v1;
+    uz[3] = top ? o2 : v2;
+  } else {
+    uz[0] = top ? v1 : o1;
+    uz[1] = top ? o1 : v1;
+  }
+  const int j0 = top ? 0 : P;  // this lane's interface rows: s-P .. s-1 (top), s .. s+P-1
+  double z[P];
+#pragma unroll
+  for (int jj = 0; jj < P; ++jj) {
+    const int j = j0 + jj;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < NZ; ++q) v = fma(minv[j * NZ + q], uz[q], v);
+    z[jj] = v;
+    st_stream(y + (int64_t)(s - P + j) * ld, v);
+  }
+
+  // ---- backward: rows s-P-1 .. 0 (top) or s+P .. N-1 (bottom)
+  const int nbk = top ? s - P : N - s - P;
+  const int TB = s > N - s ? s - P : N - s - P;
+  auto issue_b = [&](int t) {
+    if (t < nbk) cp_async<8>(rs + (t & (D - 1)) * T, y + (int64_t)(top ? s - P - 1 - t : s + P + t) * ld);
+    cp_commit();
+  };
+#pragma unroll
+  for (int t = 0; t < D; ++t) issue_b(t);
+  // the two nearest solved rows: x_{i+1}, x_{i+2} (top) or x_{i-1}, x_{i-2} (bottom)
+  double x1 = top ? z[0] : z[P - 1];
+  double x2 = P == 2 ? (top ? z[P - 1] : z[0]) : 0.0;
+  for (int t0 = 0; t0 < TB; t0 += K) {
+    cp_wait<D - K>();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int t = t0 + j;
+      if (t < nbk) {
+        const int i = top ? s - P - 1 - t : s + P + t;
+        const double xi = A::step<P, true>(bw + W * i, rs[(t & (D - 1)) * T], x1, x2);
+        st_stream(y + (int64_t)i * ld, xi);
+        x2 = x1;
+        x1 = xi;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) issue_b(t0 + D + j);
+  }
+  cp_wait<0>();
+}
+
+template <int P>
+__global__ void __launch_bounds__(1024)
+sweep_two_ended_kernel(const double* __restrict__ img, int N, int s, int64_t M, int64_t ld, const double* rhs,
+                       double* x, int64_t ntiles, unsigned ring_off) {
+  constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* cs = reinterpret_cast<double*>(smem_raw);
+  stage(cs, img, 2 * W * N + 4 * P * P);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < ntiles;
+       tile += (int64_t)gridDim.x * nw)
+    two_ended_tile<P>(cs, cs + W * N, cs + 2 * W * N, N, s, M, ld, rhs, x, tile, smem_raw + ring_off);
+}
+
 // The periodic correction data of a factor for an arithmetic policy: (w_i, -z_i)
 // rows of op `o` and the scalars alpha, beta as coefficients.
 template <class A>
@@ -194,6 +331,32 @@ int launch_staged(const sb_factor* f, const typename A::C* coef, const void* rhs
   }
 }
 
+// The two-ended sweeps of op (A or A^T); *applied = false (nothing launched, SB_OK)
+// where they do not apply: no image (periodic factor, N < 4P, a zero pivot or a
+// singular interface), or image and ring beyond one CTA's shared memory.
+int launch_two_ended(const sb_factor* f, Op op, const void* rhs, void* x, int64_t M, int64_t ld,
+                     const SweepShape& shape, cudaStream_t stream, bool* applied) {
+  *applied = false;
+  const double* img = f->two_img[op == OP_PRIMAL ? 0 : 1];
+  if (img == nullptr) return SB_OK;
+  const int N = (int)f->N, P = f->P, threads = shape.threads;
+  if (threads < 32 || threads > 1024 || threads % 32 != 0)
+    return fail(SB_ERR_INVALID_ARG, "threads per CTA must be a multiple of 32 in [32, 1024] for the two-ended sweeps");
+  const size_t ring_off = (((size_t)2 * (P + 1) * N + 4 * P * P) * sizeof(double) + 15) / 16 * 16;
+  const size_t smem = ring_off + (size_t)kTwoRows * threads * sizeof(double);
+  if (smem > (size_t)kMaxDynSmem) return SB_OK;
+  *applied = true;
+  auto k = P == 1 ? sweep_two_ended_kernel<1> : sweep_two_ended_kernel<2>;
+  int nb = 0;
+  SB_TRY(kernel_occupancy(reinterpret_cast<const void*>(k), f->device, threads, smem, &nb));
+  if (shape.ctas_per_sm > 0) nb = std::min(nb, shape.ctas_per_sm);
+  const int64_t ntiles = (M + 15) / 16;  // 16 systems per warp
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nb * sm_count(f->device)));
+  k<<<(unsigned)grid, threads, smem, stream>>>(img, N, f->two_s, M, ld, static_cast<const double*>(rhs),
+                                              static_cast<double*>(x), ntiles, (unsigned)ring_off);
+  return cuda_check(cudaGetLastError(), "two-ended sweep kernel launch");
+}
+
 template <class A, int P, bool F_ONE, bool B_ONE, typename TI, typename TO, int CYC>
 int launch_spt(const sb_factor* f, const typename A::C* coef, const void* rhs, void* x, int64_t M,
                int64_t ld, const SweepShape& shape, cudaStream_t stream, int op) {
@@ -288,6 +451,15 @@ int launch_sweep(const sb_factor* f, Op op, const void* rhs, sb_dtype rhs_dtype,
     // sweeps run with their default shape
     return launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, default_shape(f, arith),
                         stream);
+  }
+  if (shape.algo == SB_ALGO_TWO_ENDED) {
+    if (arith == SB_ARITH_NATIVE && rhs_dtype == SB_F64 && x_dtype == SB_F64) {
+      bool applied = false;
+      const int rc = launch_two_ended(f, op, rhs, x, M, ld, shape, stream, &applied);
+      if (rc != SB_OK || applied) return rc;
+    }
+    // where the two-ended sweeps do not apply, the sequential ones with the default shape
+    return launch_sweep(f, op, rhs, rhs_dtype, x, x_dtype, M, ld, arith, default_shape(f, arith), stream);
   }
   if (shape.algo != SB_ALGO_SEQUENTIAL && shape.algo != SB_ALGO_STAGED)
     return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape.algo);

@@ -69,7 +69,7 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
   clear_error();
   if (!f || !shape) return fail(SB_ERR_INVALID_ARG, "NULL argument");
   if (shape->algorithm != SB_ALGO_SEQUENTIAL && shape->algorithm != SB_ALGO_PARTITIONED &&
-      shape->algorithm != SB_ALGO_STAGED)
+      shape->algorithm != SB_ALGO_STAGED && shape->algorithm != SB_ALGO_TWO_ENDED)
     return fail(SB_ERR_INVALID_ARG, "unknown algorithm %d", shape->algorithm);
   if (shape->ctas_per_sm < 0 || shape->ctas_per_sm > 32)
     return fail(SB_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 32]");
@@ -78,12 +78,12 @@ int sb_shape_set(const sb_factor* f, sb_arith arith, sb_dtype rhs_dtype, sb_dtyp
       return fail(SB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512]");
     if (shape->systems_per_thread != 1 && shape->systems_per_thread != 2)
       return fail(SB_ERR_INVALID_ARG, "systems_per_thread must be 1 or 2");
-  } else if (shape->algorithm == SB_ALGO_STAGED) {
-    const int cap = arith == SB_ARITH_DF32 ? 512 : 1024;
+  } else if (shape->algorithm == SB_ALGO_STAGED || shape->algorithm == SB_ALGO_TWO_ENDED) {
+    const int cap = (arith == SB_ARITH_DF32 && shape->algorithm == SB_ALGO_STAGED) ? 512 : 1024;
     if (shape->threads < 32 || shape->threads > cap || shape->threads % 32 != 0)
-      return fail(SB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, %d] for the staged sweeps", cap);
+      return fail(SB_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, %d] for this algorithm", cap);
     if (shape->systems_per_thread != 1)
-      return fail(SB_ERR_INVALID_ARG, "the staged sweeps take systems_per_thread = 1");
+      return fail(SB_ERR_INVALID_ARG, "the staged and two-ended sweeps take systems_per_thread = 1");
   } else {
     if (part_variant(shape->threads) < 0 && shape->threads != kPart64Threads)
       return fail(SB_ERR_INVALID_ARG, "the partitioned solve runs 128, 256, 512 or 1024 threads per CTA");
@@ -139,6 +139,15 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
       s.threads = threads;
       s.ctas_per_sm = 0;
       s.algo = SB_ALGO_STAGED;
+      cands.push_back(s);
+    }
+  if (f->two_img[op == OP_PRIMAL ? 0 : 1] && arith == SB_ARITH_NATIVE && rhs_dtype == SB_F64 &&
+      x_dtype == SB_F64)
+    for (int threads : {256, 512, 768, 1024}) {
+      SweepShape s;
+      s.threads = threads;
+      s.ctas_per_sm = 0;
+      s.algo = SB_ALGO_TWO_ENDED;
       cands.push_back(s);
     }
   if (partitioned64_applies(f, op, rhs_dtype, x_dtype, M, arith)) {

@@ -207,7 +207,7 @@ def test_fallback_where_the_partition_does_not_apply(env, case):
 def test_bad_partitioned_shapes_rejected(env):
     sb, _ = env
     fac = factor(sb, synth.random_penta_diagonals(seed=1, N=256))
-    for bad in [(384, 0, 1, 1), (1024, 2, 1, 1), (512, 0, 2, 1), (1024, 0, 1, 3)]:
+    for bad in [(384, 0, 1, 1), (1024, 2, 1, 1), (512, 0, 2, 1), (1024, 0, 1, 9)]:
         with pytest.raises(sb.SbError):
             sb.sb_shape_set(fac, bad)
 
@@ -220,7 +220,7 @@ def test_autotune_fp32_headline_shape_is_correct(env):
     rhs = synth.torch_uniform(seed=3, N=N, M=M, lo=-1.0, hi=1.0, dtype=torch.float32, device="cuda")
     x = torch.empty_like(rhs)
     best, ms = sb.sb_autotune(fac, rhs, x)
-    assert best[3] in (0, 1, 2) and ms > 0
+    assert best[3] in (0, 1, 2, 3) and ms > 0
     assert sb.sb_shape_get(fac, rhs_dtype=sb.SB_F32, x_dtype=sb.SB_F32) == best
     sb.sb_solve_batched(fac, rhs, x)
     torch.cuda.synchronize()
