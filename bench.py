@@ -215,7 +215,7 @@ def run_reference(args):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("sweep.cu", "sweep_tile.cuh", "arith.cuh"):
+    for name in ("sweep.cu", "sweep_tile.cuh", "arith.cuh", "two_ended.h"):
         with open(os.path.join(ROOT, "paper_2107_05395_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -742,7 +742,14 @@ def run_ours(args):
     # pick the launch shape of each arithmetic mode with the library's autotuner
     shapes = {}
     for mode in ("native", "df32"):
-        shapes[mode] = sb.sb_autotune(fac, rhs, x, arith=mode)
+        if mode == arith and args.shape:
+            # a pinned shape (e.g. for a profiler run, whose serialised launches can
+            # change the autotuner's ranking)
+            shp = tuple(int(v) for v in args.shape.split(","))
+            sb.sb_shape_set(fac, shp, arith=mode)
+            shapes[mode] = (shp, None)
+        else:
+            shapes[mode] = sb.sb_autotune(fac, rhs, x, arith=mode)
 
     def step():
         sb.sb_solve_batched_ex(fac, rhs, x, arith=arith, stream=stream)
@@ -965,6 +972,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arith", choices=["native", "df32"], default="native")
     ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
+    ap.add_argument("--shape", default="",
+                    help="threads,ctas_per_sm,systems_per_thread,algorithm of the headline solve instead of "
+                         "the autotuner's choice")
     ap.add_argument("--extras", default="", help="comma-separated names of the extras to run (default: all)")
     ap.add_argument("--coarsening-systems", type=int, default=1 << 16,
                     help="simulations per domain in the coarsening extra (the paper: 1048576)")
