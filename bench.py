@@ -855,6 +855,37 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, device="cuda")
 
+    # the host link on this machine, for reading e2e: the same pinned buffers copied
+    # whole, one direction at a time and both at once (copy engines, no kernel)
+    def link_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(reps):
+            fn()
+        l1.record(stream)
+        torch.cuda.synchronize()
+        return l0.elapsed_time(l1) / reps
+
+    side = torch.cuda.Stream()
+
+    def both():
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            h_x.copy_(x, non_blocking=True)
+        with torch.cuda.stream(stream):
+            rhs.copy_(h_rhs, non_blocking=True)
+        stream.wait_stream(side)
+
+    with torch.cuda.stream(stream):
+        nbytes = N_ROWS * M_SYS * 8
+        link = {"h2d": nbytes / link_ms(lambda: rhs.copy_(h_rhs, non_blocking=True)) / 1e6,
+                "d2h": nbytes / link_ms(lambda: h_x.copy_(x, non_blocking=True)) / 1e6,
+                "both": 2 * nbytes / link_ms(both) / 1e6}
+    link = {k: round(v, 1) for k, v in link.items()}
+    link["e2e_bound_solves_per_s"] = round(link["both"] * 1e9 / (2 * nbytes), 1)
+
     extras = {}
     # the paper-workload extras run on one GPU (a multi-GPU run measures the scaling
     # of the headline step only, unless extras are named explicitly)
@@ -940,7 +971,8 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT,
-                "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8},
+                "h2d_bytes_per_step": elts * 8, "d2h_bytes_per_step": elts * 8,
+                "host_link_gbs": link},
         "extras": {
             **extras,
             "solve_fp32": fp32_extra,

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "sb_internal.h"
@@ -33,6 +34,7 @@ struct Groups {
   int G;
   int cta_begin[kMaxGroups + 1];
   const CT* coef[kMaxGroups];   // sweep rows [forward | backward]
+  const CT* rcoef[kMaxGroups];  // the same for J A J, at A's row indices (fused refinement only)
   const void* arow[kMaxGroups]; // A row by row (refinement passes only)
   int N[kMaxGroups];
   int64_t M[kMaxGroups], ld[kMaxGroups], ntiles[kMaxGroups];
@@ -70,9 +72,9 @@ grouped_sweep_kernel(const __grid_constant__ Groups<typename A::C, TI, TO> a) {
 
 // ------------------------------------------------------- refinement pass
 
-// FP64 -> FP32 by truncation with integer operations (the sign, exponent and top
-// 23 fraction bits); exact FP64 conversion outside the integer path's range.
-__device__ __forceinline__ float narrow_trunc(double v) { return double_to_df(v).h; }
+// FP64 residual -> FP32 right-hand side of the correction sweep (truncation with
+// integer operations; see f64_to_f32_trunc).
+__device__ __forceinline__ float narrow_trunc(double v) { return f64_to_f32_trunc(v); }
 
 template <bool DFRES>
 struct Residual;
@@ -470,6 +472,239 @@ grouped_refined_solve_kernel(const __grid_constant__ Groups<float, TB, double> a
   }
 }
 
+// ------------------------------------------------ fused refinement passes
+//
+// The same solve with each correction pass's residual and forward sweep merged
+// into the backward sweep of the pass before it, which already delivers x row by
+// row.  For that, pass k eliminates from the top (the rows of A = LU) when k is
+// even and from the bottom (the rows of J A J, J the exchange matrix) when k is
+// odd, so that its forward sweep runs in the direction in which pass k-1's backward
+// sweep produces x:
+//   pass 0:              forward sweep of b into g (rows 0 .. N-1)
+//   merged pass k >= 1:  pass k-1's backward sweep of g gives d_i and
+//                        x_{k-1,i} = x_{k-2,i} + d_i (stored); P rows behind it the
+//                        residual r_j = b_j - (A x_{k-1})_j and pass k's forward step
+//                        at row j, into the row of g that was read P iterations before
+//   last:                pass n's backward sweep, x_n = x_{n-1} + d.
+// Bytes per element with n = 2: 4 + 4, then 4 + 8 + 4 + 4 (k = 1: x_0 is not read),
+// 4 + 8 + 8 + 4 + 4 and 4 + 8 + 8: 76, against 92 for separate passes.  The FP64
+// work (the residuals and the additions to x) is the same.  Each lane copies and
+// reads only its own system's values, as in the staged passes above.
+
+// One merged pass (k >= 1): DOWN when pass k-1 eliminated from the top, i.e. its
+// backward sweep runs from row N-1 down.  bw: backward rows of pass k-1; fw: forward
+// rows of pass k (both at A's row indices); FIRST: k == 1 (x_0 = d, nothing to add).
+template <int P, bool DFRES, typename TB, int D, bool DOWN, bool FIRST>
+__device__ __forceinline__ void fused_merged_pass(const float* bw, const float* fw,
+                                                  const typename Residual<DFRES>::AC* arow, int N, int64_t ld,
+                                                  const TB* bp, double* xp, float* gp, double* rx, float* rg,
+                                                  TB* rb, int T) {
+  using RS = Residual<DFRES>;
+  using X = typename RS::X;
+  using F = NativeArith<float>;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  constexpr int K = kStageBatch;
+  // iteration s takes row(s) of g (and of x_{k-2}) and row(s - P) of b
+  auto row = [&](int s) { return DOWN ? N - 1 - s : s; };
+  auto issue = [&](int s) {
+    const int sl = (s & (D - 1)) * T;
+    if (s < N) {
+      const int i = row(s);
+      cp_async<4>(rg + sl, gp + (int64_t)i * ld);
+      if (!FIRST) cp_async<8>(rx + sl, xp + (int64_t)i * ld);
+    }
+    if (s >= P && s < N + P) cp_async<sizeof(TB)>(rb + sl, bp + (int64_t)row(s - P) * ld);
+    cp_commit();
+  };
+  // window x_{j-P} .. x_{j+P} of the residual's row j: the newest value enters at
+  // the low end going down and at the high end going up; rows outside 0..N-1 are 0
+  X xw[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) xw[q] = RS::in(0.0);
+  auto push = [&](double v) {
+    if constexpr (DOWN) {
+#pragma unroll
+      for (int q = NB - 1; q > 0; --q) xw[q] = xw[q - 1];
+      xw[0] = RS::in(v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NB - 1; ++q) xw[q] = xw[q + 1];
+      xw[NB - 1] = RS::in(v);
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < D; ++s) issue(s);
+  float d1 = 0.f, d2 = 0.f, u1 = 0.f, u2 = 0.f;
+  for (int s0 = 0; s0 < N + P; s0 += K) {
+    cp_wait<D - K>();  // the groups of iterations s0 .. s0+K-1 are complete
+    float r[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int s = s0 + q;
+      const int sl = (s & (D - 1)) * T;
+      double xi = 0.0;
+      if (s < N) {
+        const int i = row(s);
+        const float d = F::step<P, true>(bw + W * i, rg[sl], d1, d2);
+        d2 = d1;
+        d1 = d;
+        xi = FIRST ? widen_f32(d) : rx[sl] + widen_f32(d);
+        st_stream(xp + (int64_t)i * ld, xi);
+      }
+      push(xi);
+      r[q] = (s >= P && s < N + P) ? RS::template eval<NB>(arow + NB * row(s - P), xw, rb[sl]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int s = s0 + q;
+      if (s >= P && s < N + P) {
+        const int j = row(s - P);
+        const float u = F::step<P, false>(fw + W * j, r[q], u1, u2);
+        gp[(int64_t)j * ld] = u;
+        u2 = u1;
+        u1 = u;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) issue(s0 + D + q);  // refills the K slots used above
+  }
+  cp_wait<0>();
+  __threadfence_block();  // the stores of g and x before the copies of the next pass
+}
+
+// The last backward sweep: x_i = x_{n-1,i} + d_i (x_i = d_i when FIRST, n = 0).
+template <int P, int D, bool DOWN, bool FIRST>
+__device__ __forceinline__ void fused_last_pass(const float* bw, int N, int64_t ld, double* xp, float* gp,
+                                                double* rx, float* rg, int T) {
+  using F = NativeArith<float>;
+  constexpr int W = P + 1;
+  constexpr int K = kStageBatch;
+  auto row = [&](int s) { return DOWN ? N - 1 - s : s; };
+  auto issue = [&](int s) {
+    const int sl = (s & (D - 1)) * T;
+    if (s < N) {
+      const int i = row(s);
+      cp_async<4>(rg + sl, gp + (int64_t)i * ld);
+      if (!FIRST) cp_async<8>(rx + sl, xp + (int64_t)i * ld);
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < D; ++s) issue(s);
+  float d1 = 0.f, d2 = 0.f;
+  for (int s0 = 0; s0 < N; s0 += K) {
+    cp_wait<D - K>();
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int s = s0 + q;
+      if (s < N) {
+        const int sl = (s & (D - 1)) * T;
+        const int i = row(s);
+        const float d = F::step<P, true>(bw + W * i, rg[sl], d1, d2);
+        d2 = d1;
+        d1 = d;
+        st_stream(xp + (int64_t)i * ld, FIRST ? widen_f32(d) : rx[sl] + widen_f32(d));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) issue(s0 + D + q);
+  }
+  cp_wait<0>();
+}
+
+// Shared-memory bytes of the fused form's ring: D slots per thread of an FP64 value,
+// an FP32 intermediate and a right-hand-side value.
+template <typename TB>
+constexpr size_t fused_ring_bytes(int D, int threads) {
+  return (size_t)D * threads * (sizeof(double) + sizeof(float) + sizeof(TB));
+}
+
+// cf: rows [forward | backward] of A = LU; cr: the same of J A J at A's row indices.
+template <int P, bool DFRES, typename TB, int D>
+__device__ __forceinline__ void refine_fused_tile(const float* cf, const float* cr,
+                                                  const typename Residual<DFRES>::AC* arow, int N, int64_t M,
+                                                  int64_t ld, const TB* b, double* x, float* g, int64_t tile,
+                                                  unsigned char* ring, int n_refine) {
+  using F = NativeArith<float>;
+  constexpr int W = P + 1;
+  static_assert((D & (D - 1)) == 0 && D % kStageBatch == 0, "the ring length is a power of two and a multiple of K");
+  const int64_t m = tile * 32 + (threadIdx.x & 31);
+  if (m >= M) return;
+  const TB* bp = b + m;
+  double* xp = x + m;
+  float* gp = g + m;
+  const int T = blockDim.x;
+  double* rx = reinterpret_cast<double*>(ring) + threadIdx.x;
+  float* rg = reinterpret_cast<float*>(ring + (size_t)D * T * sizeof(double)) + threadIdx.x;
+  TB* rb = reinterpret_cast<TB*>(ring + (size_t)D * T * (sizeof(double) + sizeof(float))) + threadIdx.x;
+  __threadfence_block();  // this thread's stores of an earlier tile before the copies below
+
+  // pass 0: forward sweep of b (from the top) into g
+  {
+    auto issue = [&](int k) {
+      if (k < N) cp_async<sizeof(TB)>(rb + (k & (D - 1)) * T, bp + (int64_t)k * ld);
+      cp_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) issue(k);
+    float u1 = 0.f, u2 = 0.f;
+    for (int i = 0; i < N; ++i) {
+      cp_wait<D - 1>();
+      const float u = F::step<P, false>(cf + W * i, Conv<F, TB>::in(rb[(i & (D - 1)) * T]), u1, u2);
+      gp[(int64_t)i * ld] = u;
+      u2 = u1;
+      u1 = u;
+      issue(i + D);
+    }
+    cp_wait<0>();
+    __threadfence_block();
+  }
+  const float* lu_f = cf;
+  const float* lu_b = cf + W * N;
+  const float* ul_f = cr;
+  const float* ul_b = cr + W * N;
+  for (int k = 1; k <= n_refine; ++k) {
+    if (k == 1)
+      fused_merged_pass<P, DFRES, TB, D, true, true>(lu_b, ul_f, arow, N, ld, bp, xp, gp, rx, rg, rb, T);
+    else if (k & 1)
+      fused_merged_pass<P, DFRES, TB, D, true, false>(lu_b, ul_f, arow, N, ld, bp, xp, gp, rx, rg, rb, T);
+    else
+      fused_merged_pass<P, DFRES, TB, D, false, false>(ul_b, lu_f, arow, N, ld, bp, xp, gp, rx, rg, rb, T);
+  }
+  if (n_refine == 0)
+    fused_last_pass<P, D, true, true>(lu_b, N, ld, xp, gp, rx, rg, T);
+  else if (n_refine & 1)
+    fused_last_pass<P, D, false, false>(ul_b, N, ld, xp, gp, rx, rg, T);
+  else
+    fused_last_pass<P, D, true, false>(lu_b, N, ld, xp, gp, rx, rg, T);
+}
+
+template <int P, bool DFRES, typename TB, int D>
+__global__ void __launch_bounds__(kStagedThreads, 1)
+grouped_refined_fused_kernel(const __grid_constant__ Groups<float, TB, double> a, int n_refine,
+                             unsigned ring_off) {
+  using AC = typename Residual<DFRES>::AC;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = group_of(a.cta_begin, a.G);
+  const int N = a.N[g];
+  AC* as = reinterpret_cast<AC*>(smem_raw);  // A rows first (8-byte aligned)
+  float* cs = reinterpret_cast<float*>(as + NB * N);
+  float* crs = cs + 2 * W * N;
+  stage(as, static_cast<const AC*>(a.arow[g]), NB * N);
+  stage(cs, a.coef[g], 2 * W * N);
+  stage(crs, a.rcoef[g], 2 * W * N);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
+  for (int64_t tile = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
+       tile < a.ntiles[g]; tile += (int64_t)ctas * nw)
+    refine_fused_tile<P, DFRES, TB, D>(cs, crs, as, N, a.M[g], a.ld[g], a.rhs[g], a.x[g], a.work[g], tile,
+                                       smem_raw + ring_off, n_refine);
+}
+
 // ---------------------------------------------------- refined time step
 
 // Right-hand side of a time step for one tile, in FP64, in the same order of
@@ -578,11 +813,11 @@ constexpr int kThreads = 256;
 template <typename K>
 int resident_ctas(K kernel, int device, size_t smem, int* total, int threads = kThreads) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, size_t>, int> cache;
+  static std::map<std::tuple<const void*, size_t, int>, int> cache;
   int nb = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(reinterpret_cast<const void*>(kernel), smem);
+    auto key = std::make_tuple(reinterpret_cast<const void*>(kernel), smem, threads);
     auto it = cache.find(key);
     if (it != cache.end()) {
       nb = it->second;
@@ -666,6 +901,39 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
                               (size_t)2 * (P + 1) * f[g]->N * sizeof(float));
   }
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "a group's factors exceed shared memory");
+  // the fused passes (FP32 right-hand sides) when every group has the rows of J A J
+  // and both coefficient sets and a ring of 16, else 8, rows fit in shared memory
+  if constexpr (std::is_same<TB, float>::value) {
+    bool fused = n_refine > 0;
+    size_t fsmem = 0;
+    for (int g = 0; g < a.G; ++g) {
+      fused = fused && f[g]->coef32_rev != nullptr;
+      a.rcoef[g] = f[g]->coef32_rev;
+      fsmem = std::max(fsmem, (size_t)(2 * P + 1) * f[g]->N * sizeof(AC) +
+                                  (size_t)4 * (P + 1) * f[g]->N * sizeof(float));
+    }
+    const size_t foff = (fsmem + 15) / 16 * 16;
+    if (fused && foff < (size_t)kMaxDynSmem) {
+      // a 16-row ring with as many threads (256 to 512) as fit beside the
+      // coefficients, else an 8-row ring; else the passes below
+      const size_t room = (size_t)kMaxDynSmem - foff;
+      auto fit = [&](int D) { return (int)std::min<size_t>(kStagedThreads, room / fused_ring_bytes<TB>(D, 1) / 32 * 32); };
+      int D = 16, threads = fit(16);
+      if (threads < 256) {
+        D = 8;
+        threads = fit(8);
+      }
+      if (threads >= 256) {
+        const size_t total_smem = foff + fused_ring_bytes<TB>(D, threads);
+        auto k = D == 16 ? grouped_refined_fused_kernel<P, DFRES, TB, 16> : grouped_refined_fused_kernel<P, DFRES, TB, 8>;
+        int total = 0;
+        SB_TRY(resident_ctas(k, f[0]->device, total_smem, &total, threads));
+        const int grid = plan(a, f, total);
+        k<<<grid, threads, total_smem, stream>>>(a, n_refine, (unsigned)foff);
+        return cuda_check(cudaGetLastError(), "fused refined solve launch");
+      }
+    }
+  }
   // the staged passes when their ring fits beside the coefficients
   const size_t ring_off = (smem + 15) / 16 * 16;
   const bool staged = n_refine > 0 && ring_off + stage_ring_bytes<TB>(kStagedThreads) <= (size_t)kMaxDynSmem;

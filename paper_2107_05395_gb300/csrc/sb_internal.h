@@ -127,6 +127,12 @@ struct sb_factor {
   double* two_img[2] = {nullptr, nullptr};
   int two_s = 0;
   float* arowdf = nullptr;   // device: the same as (hi, lo) FP32 pairs
+  // device: FP32 sweep rows [forward | backward] of the primal solve by way of the
+  // reversed matrix J A J (J the exchange matrix), row i holding the coefficients
+  // used at A's row i: the forward sweep runs from row N-1 down to row 0 and the
+  // backward sweep from row 0 up.  Used by refinement passes that alternate their
+  // direction; null for periodic factors or when J A J has a zero pivot.
+  float* coef32_rev = nullptr;
   std::vector<double> h_coef;  // host copy of coef64
   std::vector<double> h_diag;  // host copy of diag64 (of A' for a periodic factor)
   // Periodic tridiagonal (section 3.3): the factors above are those of A' and each

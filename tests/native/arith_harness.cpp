@@ -17,6 +17,10 @@ void h_double_to_df(const double* v, float* h, float* l, long n) {
   }
 }
 
+void h_f64_to_f32_trunc(const double* v, float* out, long n) {
+  for (long i = 0; i < n; ++i) out[i] = f64_to_f32_trunc(v[i]);
+}
+
 void h_df_to_double(const float* h, const float* l, double* out, long n) {
   for (long i = 0; i < n; ++i) out[i] = df_to_double(df{h[i], l[i]});
 }

@@ -35,6 +35,7 @@ def H(tmp_path_factory):
     L.h_df_step.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp, fp, fp, fp]
     L.h_df_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, dp, dp, dp]
     L.h_dmul_int.argtypes = [dp, dp, dp, ctypes.c_long]
+    L.h_f64_to_f32_trunc.argtypes = [dp, fp, ctypes.c_long]
     return L
 
 
@@ -60,6 +61,33 @@ def join(H, h, l):
 
 def ulp32(h):
     return np.spacing(np.abs(np.float32(h))).astype(np.float64)
+
+
+def test_residual_truncation_to_fp32(H):
+    """f64_to_f32_trunc (the refinement residual's FP64 -> FP32 step, integer
+    operations only): truncation toward zero over FP32's normal range, a signed zero
+    below 2^-126 (exact zeros included), an infinity from 2^128 up, NaNs kept.  The reference
+    rounds to nearest with NumPy and steps back toward zero where that went past
+    |v|."""
+    rng = np.random.default_rng(5)
+    n = 200000
+    v = rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-140, 135, n).astype(np.float64))
+    v *= np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    v = np.concatenate([v, [0.0, -0.0, np.inf, -np.inf, np.nan, 2.0 ** -126, -(2.0 ** -126),
+                            np.nextafter(2.0 ** -126, 0.0), np.nextafter(2.0 ** 128, 0.0),
+                            float(np.finfo(np.float32).max), 1.0, -1.0 - 2.0 ** -40]])
+    out = np.empty(v.shape, np.float32)
+    H.h_f64_to_f32_trunc(_p(v, ctypes.c_double), _p(out, ctypes.c_float), v.size)
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float32)
+    past = np.abs(ref.astype(np.float64)) > np.abs(v)
+    ref[past] = np.nextafter(ref[past], np.float32(0.0))
+    tiny = np.abs(v) < 2.0 ** -126
+    ref[tiny] = np.copysign(np.float32(0.0), v[tiny]).astype(np.float32)
+    huge = np.abs(v) >= 2.0 ** 128  # beyond FP32's range: rounded, i.e. infinite
+    ref[huge] = np.copysign(np.float32(np.inf), v[huge]).astype(np.float32)
+    assert np.array_equal(out.view(np.uint32)[~np.isnan(v)], ref.view(np.uint32)[~np.isnan(v)])
+    assert np.all(np.isnan(out[np.isnan(v)]))
 
 
 def test_split_is_accurate_and_normalised(H):

@@ -55,6 +55,57 @@ def test_refinement_contracts_to_fp64_accuracy(env, kind, N, M, ld, residual):
     assert errs[1] <= max(errs[0] * 1e-2, 1e-13) and errs[2] <= max(errs[1], 1e-13), errs
 
 
+@pytest.mark.parametrize("residual", ["native", "df32"])
+@pytest.mark.parametrize("kind,N,M", [("tri", 37, 70), ("penta", 37, 70), ("tri", 3, 33), ("penta", 6, 33),
+                                      ("tri", 2048, 100), ("penta", 1400, 65), ("penta", 2000, 65),
+                                      ("penta", 2400, 40)])
+def test_refinement_passes_alternate_direction(env, kind, N, M, residual):
+    """FP32 right-hand sides take the fused passes: pass k eliminates from the top
+    (A = LU) for even k and from the bottom (the rows of J A J) for odd k, each
+    correction pass merged into the backward sweep before it.  One to four passes
+    cover both directions of the merged and of the last pass.  Shared memory holds
+    the coefficients and a ring per thread: 16 rows for 512 threads up to N = 37,
+    448 threads for tri N = 2048, 416 for penta N = 1400; 8 rows (416 threads) for
+    penta N = 2000; penta N = 2400 leaves no room and runs the separate passes.
+    The random matrices are nonsymmetric, so a wrong reversal of J A J's diagonals
+    stops the contraction."""
+    sb, torch = env
+    fac, ref_fn = make(sb, kind, N, seed=N + 11)
+    ld = M + 3
+    b32 = synth.rhs_uniform(seed=N + 1, N=N, M=M, ld=ld, dtype=np.float32, pad_value=9.0)
+    ref = ref_fn(b32[:, :M].astype(np.float64))
+    d_b = to_dev(b32, torch)
+    work = torch.full((N, ld), -1.0, dtype=torch.float32, device="cuda")
+    errs = []
+    for n in (0, 1, 2, 3, 4):
+        x = torch.full((N, ld), 7.0, dtype=torch.float64, device="cuda")
+        sb.sb_solve_batched_refined(fac, d_b, x, n_refine=n, residual_arith=residual, work=work, M=M)
+        torch.cuda.synchronize()
+        out = to_host(x)
+        assert np.all(out[:, M:] == 7.0)
+        errs.append(np.max(relerr_per_system(out[:, :M], ref)))
+    assert errs[0] <= 2e-5, errs
+    assert errs[1] <= max(errs[0] * 1e-2, 1e-13), errs
+    assert max(errs[2:]) <= 1e-10, errs
+
+
+def test_refinement_without_reversed_rows(env):
+    """A = [[1, 1], [1, 0]] factors from the top, but J A J = [[0, 1], [1, 1]] has a
+    zero first pivot: the solve then runs the passes without alternating."""
+    sb, torch = env
+    a, b, c = np.array([0.0, 1.0]), np.array([1.0, 0.0]), np.array([1.0, 0.0])
+    fac = sb.sb_factor_shared_tri(a, b, c)
+    M = 40
+    b32 = synth.rhs_uniform(seed=5, N=2, M=M, ld=M, dtype=np.float32, pad_value=0.0)
+    ref = np.linalg.solve(np.array([[1.0, 1.0], [1.0, 0.0]]), b32.astype(np.float64))
+    work = torch.zeros((2, M), dtype=torch.float32, device="cuda")
+    for n in (1, 2, 3):
+        x = torch.zeros((2, M), dtype=torch.float64, device="cuda")
+        sb.sb_solve_batched_refined(fac, to_dev(b32, torch), x, n_refine=n, work=work)
+        torch.cuda.synchronize()
+        assert np.max(relerr_per_system(to_host(x), ref)) <= 1e-12, n
+
+
 @pytest.mark.parametrize("arith,rt,xt,tol", [("native", "f64", "f64", 1e-12), ("df32", "f64", "f64", 1e-12),
                                              ("df32", "f32", "f64", 1e-12), ("native", "f32", "f32", 2e-5)])
 def test_groups_without_refinement(env, arith, rt, xt, tol):
