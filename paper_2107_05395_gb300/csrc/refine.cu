@@ -705,6 +705,211 @@ grouped_refined_fused_kernel(const __grid_constant__ Groups<float, TB, double> a
                                        smem_raw + ring_off, n_refine);
 }
 
+// ------------------------------------------- paired tiles, two refinements
+//
+// With two correction passes a tile goes through four sweeps: pass 0's forward
+// sweep (up, no FP64 work), the first merged pass (down, 3 FP64 operations per
+// element for a tridiagonal A), the second (up, 4) and the last backward sweep
+// (down, 1).  A warp whose tiles all sit in the same sweep leaves the FP64 pipe
+// idle in the first and the last one.  Here a warp carries two tiles two sweeps
+// apart, so every loop runs sweeps 0 and 2, or 1 and 3, of two different tiles
+// side by side: both in the same direction, with 4 FP64 operations and 36 bytes
+// per element pair in every loop.  Tile k of the warp runs its sweep p in step
+// 2k + p; steps 0, 1 and the last two carry a single tile.
+
+struct TileRef {
+  const float* b;
+  double* x;
+  float* g;
+  bool ok;  // this lane's system exists (the last tile may be ragged)
+};
+
+// Shared-memory bytes of the paired form's ring: D slots per thread of an FP64
+// value and three FP32 values.
+constexpr size_t pair_ring_bytes(int D, int threads) {
+  return (size_t)D * threads * (sizeof(double) + 3 * sizeof(float));
+}
+
+// One step: ODD == false runs sweep 0 of tile A and sweep 2 of tile B (upwards),
+// ODD == true sweep 1 of A and sweep 3 of B (downwards).  Ring use per slot: even
+// steps b of A (f1), g and x of B (f2, rx) and B's b, P rows behind (f3); odd steps
+// g of A (f1), A's b, P rows behind (f2), g and x of B (f3, rx).
+template <int P, bool DFRES, int D, bool ODD>
+__device__ __forceinline__ void pair_step(const float* cf, const float* cr,
+                                          const typename Residual<DFRES>::AC* arow, int N, int64_t ld,
+                                          const TileRef& A, bool hasA, const TileRef& B, bool hasB, double* rx,
+                                          float* f1, float* f2, float* f3, int T) {
+  using RS = Residual<DFRES>;
+  using X = typename RS::X;
+  using F = NativeArith<float>;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  constexpr int K = kStageBatch;
+  const float* lu_f = cf;
+  const float* lu_b = cf + W * N;
+  const float* ul_f = cr;
+  const float* ul_b = cr + W * N;
+  const bool a = hasA && A.ok, b = hasB && B.ok;  // this lane copies and stores
+  auto row = [&](int s) { return ODD ? N - 1 - s : s; };
+  auto issue = [&](int s) {
+    const int sl = (s & (D - 1)) * T;
+    if (s < N) {
+      const int64_t i = row(s);
+      if (!ODD) {
+        if (a) cp_async<4>(f1 + sl, A.b + i * ld);
+        if (b) {
+          cp_async<4>(f2 + sl, B.g + i * ld);
+          cp_async<8>(rx + sl, B.x + i * ld);
+        }
+      } else {
+        if (a) cp_async<4>(f1 + sl, A.g + i * ld);
+        if (b) {
+          cp_async<4>(f3 + sl, B.g + i * ld);
+          cp_async<8>(rx + sl, B.x + i * ld);
+        }
+      }
+    }
+    if (s >= P && s < N + P) {
+      const int64_t j = row(s - P);
+      if (!ODD && b) cp_async<4>(f3 + sl, B.b + j * ld);
+      if (ODD && a) cp_async<4>(f2 + sl, A.b + j * ld);
+    }
+    cp_commit();
+  };
+  // the residual's window (of B going up, of A going down); rows outside are 0
+  X xw[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) xw[q] = RS::in(0.0);
+  auto push = [&](double v) {
+    if constexpr (ODD) {
+#pragma unroll
+      for (int q = NB - 1; q > 0; --q) xw[q] = xw[q - 1];
+      xw[0] = RS::in(v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NB - 1; ++q) xw[q] = xw[q + 1];
+      xw[NB - 1] = RS::in(v);
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < D; ++s) issue(s);
+  float ua1 = 0.f, ua2 = 0.f, da1 = 0.f, da2 = 0.f;  // tile A: forward, backward recurrences
+  float ub1 = 0.f, ub2 = 0.f, db1 = 0.f, db2 = 0.f;  // tile B
+  const bool res = ODD ? hasA : hasB;                 // the tile in a merged sweep
+  for (int s0 = 0; s0 < N + P; s0 += K) {
+    cp_wait<D - K>();  // the groups of iterations s0 .. s0+K-1 are complete
+    float r[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int s = s0 + q;
+      const int sl = (s & (D - 1)) * T;
+      double xi = 0.0;
+      if (s < N) {
+        const int64_t i = row(s);
+        if (!ODD) {
+          if (hasA) {  // A, sweep 0: forward from the top
+            const float u = F::step<P, false>(lu_f + W * i, f1[sl], ua1, ua2);
+            ua2 = ua1;
+            ua1 = u;
+            if (a) A.g[i * ld] = u;
+          }
+          if (hasB) {  // B, sweep 2: backward of pass 1 (bottom elimination), x_1 = x_0 + d
+            const float d = F::step<P, true>(ul_b + W * i, f2[sl], db1, db2);
+            db2 = db1;
+            db1 = d;
+            xi = rx[sl] + widen_f32(d);
+            if (b) st_stream(B.x + i * ld, xi);
+          }
+        } else {
+          if (hasB) {  // B, sweep 3: backward of pass 2, x_2 = x_1 + d
+            const float d = F::step<P, true>(lu_b + W * i, f3[sl], db1, db2);
+            db2 = db1;
+            db1 = d;
+            if (b) st_stream(B.x + i * ld, rx[sl] + widen_f32(d));
+          }
+          if (hasA) {  // A, sweep 1: backward of pass 0, x_0 = d
+            const float d = F::step<P, true>(lu_b + W * i, f1[sl], da1, da2);
+            da2 = da1;
+            da1 = d;
+            xi = widen_f32(d);
+            if (a) st_stream(A.x + i * ld, xi);
+          }
+        }
+      }
+      push(xi);
+      r[q] = (res && s >= P && s < N + P)
+                 ? RS::template eval<NB>(arow + NB * row(s - P), xw, ODD ? f2[sl] : f3[sl])
+                 : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const int s = s0 + q;
+      if (res && s >= P && s < N + P) {
+        const int64_t j = row(s - P);
+        if (!ODD) {  // B: pass 2's forward step (top elimination)
+          const float u = F::step<P, false>(lu_f + W * j, r[q], ub1, ub2);
+          ub2 = ub1;
+          ub1 = u;
+          if (b) B.g[j * ld] = u;
+        } else {  // A: pass 1's forward step (bottom elimination)
+          const float u = F::step<P, false>(ul_f + W * j, r[q], ua1, ua2);
+          ua2 = ua1;
+          ua1 = u;
+          if (a) A.g[j * ld] = u;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) issue(s0 + D + q);  // refills the K slots used above
+  }
+  cp_wait<0>();
+  __threadfence_block();  // the stores of g and x before the copies of the next step
+}
+
+template <int P, bool DFRES, int D>
+__global__ void __launch_bounds__(kStagedThreads, 1)
+grouped_refined_pair_kernel(const __grid_constant__ Groups<float, float, double> a, unsigned ring_off) {
+  using AC = typename Residual<DFRES>::AC;
+  constexpr int W = P + 1;
+  constexpr int NB = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = group_of(a.cta_begin, a.G);
+  const int N = a.N[g];
+  AC* as = reinterpret_cast<AC*>(smem_raw);  // A rows first (8-byte aligned)
+  float* cs = reinterpret_cast<float*>(as + NB * N);
+  float* crs = cs + 2 * W * N;
+  stage(as, static_cast<const AC*>(a.arow[g]), NB * N);
+  stage(cs, a.coef[g], 2 * W * N);
+  stage(crs, a.rcoef[g], 2 * W * N);
+  __syncthreads();
+  const int T = blockDim.x;
+  unsigned char* ring = smem_raw + ring_off;
+  double* rx = reinterpret_cast<double*>(ring) + threadIdx.x;
+  float* f1 = reinterpret_cast<float*>(ring + (size_t)D * T * sizeof(double)) + threadIdx.x;
+  float* f2 = f1 + D * T;
+  float* f3 = f2 + D * T;
+  const int nw = blockDim.x >> 5;
+  const int ctas = a.cta_begin[g + 1] - a.cta_begin[g];
+  const int64_t first = (blockIdx.x - a.cta_begin[g]) + (int64_t)ctas * (threadIdx.x >> 5);
+  const int64_t stride = (int64_t)ctas * nw;
+  const int64_t ntiles = a.ntiles[g];
+  const int64_t nt = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;  // this warp's tiles
+  const int64_t M = a.M[g], ld = a.ld[g];
+  auto ref = [&](int64_t k) {
+    const int64_t m = (first + k * stride) * 32 + (threadIdx.x & 31);
+    return TileRef{a.rhs[g] + m, a.x[g] + m, a.work[g] + m, m < M};
+  };
+  for (int64_t s = 0; nt > 0 && s < 2 * nt + 2; ++s) {
+    const int64_t ka = s >> 1, kb = ka - 1;  // tile in sweep s % 2, tile in sweep s % 2 + 2
+    const bool hasA = ka < nt, hasB = kb >= 0;
+    const TileRef A = ref(hasA ? ka : 0), B = ref(hasB ? kb : 0);
+    if (s & 1)
+      pair_step<P, DFRES, D, true>(cs, crs, as, N, ld, A, hasA, B, hasB, rx, f1, f2, f3, T);
+    else
+      pair_step<P, DFRES, D, false>(cs, crs, as, N, ld, A, hasA, B, hasB, rx, f1, f2, f3, T);
+  }
+}
+
 // ---------------------------------------------------- refined time step
 
 // Right-hand side of a time step for one tile, in FP64, in the same order of
@@ -913,6 +1118,29 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
                                   (size_t)4 * (P + 1) * f[g]->N * sizeof(float));
     }
     const size_t foff = (fsmem + 15) / 16 * 16;
+    // two refinements with the FP64 residual: tiles paired two sweeps apart, with a
+    // 16-row ring when 384 or more threads fit beside the coefficients, else an
+    // 8-row ring.  (The double-float residual leaves the FP64 pipe idle anyway and
+    // is bound by instruction issue, which the paired loops raise: it takes the
+    // single-tile form below.)
+    if (!DFRES && fused && n_refine == 2 && foff < (size_t)kMaxDynSmem) {
+      const size_t room = (size_t)kMaxDynSmem - foff;
+      auto fit = [&](int D) { return (int)std::min<size_t>(kStagedThreads, room / pair_ring_bytes(D, 1) / 32 * 32); };
+      int D = 16, threads = fit(16);
+      if (threads < 384) {
+        D = 8;
+        threads = fit(8);
+      }
+      if (threads >= 256) {
+        const size_t total_smem = foff + pair_ring_bytes(D, threads);
+        auto k = D == 16 ? grouped_refined_pair_kernel<P, false, 16> : grouped_refined_pair_kernel<P, false, 8>;
+        int total = 0;
+        SB_TRY(resident_ctas(k, f[0]->device, total_smem, &total, threads));
+        const int grid = plan(a, f, total);
+        k<<<grid, threads, total_smem, stream>>>(a, (unsigned)foff);
+        return cuda_check(cudaGetLastError(), "paired refined solve launch");
+      }
+    }
     if (fused && foff < (size_t)kMaxDynSmem) {
       // a 16-row ring with as many threads (256 to 512) as fit beside the
       // coefficients, else an 8-row ring; else the passes below

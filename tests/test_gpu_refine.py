@@ -89,6 +89,26 @@ def test_refinement_passes_alternate_direction(env, kind, N, M, residual):
     assert max(errs[2:]) <= 1e-10, errs
 
 
+@pytest.mark.parametrize("residual", ["native", "df32"])
+@pytest.mark.parametrize("kind,N", [("tri", 7), ("penta", 9)])
+def test_two_refinements_many_tiles_per_warp(env, kind, N, residual):
+    """With two refinements and the FP64 residual each warp carries two tiles two
+    sweeps apart (the double-float residual runs one tile at a time).  200003
+    systems are 6251 tiles, several per warp on every SM, the last one ragged, so the
+    steps with one tile, with two, and the odd and even tile counts per warp all run;
+    every system is checked."""
+    sb, torch = env
+    M = 200003
+    fac, ref_fn = make(sb, kind, N, seed=N + 21)
+    b32 = synth.rhs_uniform(seed=N + 2, N=N, M=M, ld=M, dtype=np.float32, pad_value=0.0)
+    ref = ref_fn(b32.astype(np.float64))
+    work = torch.empty((N, M), dtype=torch.float32, device="cuda")
+    x = torch.empty((N, M), dtype=torch.float64, device="cuda")
+    sb.sb_solve_batched_refined(fac, to_dev(b32, torch), x, n_refine=2, residual_arith=residual, work=work)
+    torch.cuda.synchronize()
+    assert np.max(relerr_per_system(to_host(x), ref)) <= 1e-10
+
+
 def test_refinement_without_reversed_rows(env):
     """A = [[1, 1], [1, 0]] factors from the top, but J A J = [[0, 1], [1, 1]] has a
     zero first pivot: the solve then runs the passes without alternating."""
