@@ -679,10 +679,13 @@ def _get(d, *keys):
     return d
 
 
-def summary(extras, fp32, df32, cpu, timeouts):
+def summary(extras, fp32, df32, cpu, timeouts, link=None, fp64_fma_per_s=None):
     """Compact numeric record of every figure the workload extras report (kept at
     the end of the JSON line): times in ms (table1 in s per 1000 steps), fractions
-    of the measured HBM peak, ratios against the plain per-step solve."""
+    of the measured HBM peak, ratios against the plain per-step solve, the host
+    link's copy rates (GB/s) beside the end-to-end figure, and the refined
+    multi-group solve against its FP64-pipe bound (8 FP64 operations per element:
+    3 FMAs per residual row and 1 addition per correction, two passes)."""
     ch = extras.get("cahn_hilliard", {})
     mg = extras.get("multigroup_refine", {})
     ro = extras.get("adjoint_rollout", {})
@@ -713,7 +716,14 @@ def summary(extras, fp32, df32, cpu, timeouts):
         "cpu_all_cores": {"value": _r(_get(cpu, "all_cores", "value")), "cores": _get(cpu, "all_cores", "cores")}
         if cpu else None,
         "partition_timeouts": timeouts,
+        "host_link_gbs": {k: link.get(k) for k in ("h2d", "d2h", "both")} if link else None,
     }
+    elts = mg.get("elements")
+    t = _get(mg, "refine2_fp64_residual", "ms_per_call")
+    if elts and t and fp64_fma_per_s:
+        bound_ms = elts * 8 / fp64_fma_per_s * 1e3
+        out["multigroup_fp64_bound_ms"] = _r(bound_ms)
+        out["multigroup_of_fp64_bound"] = _r(bound_ms / t)
     return out
 
 
@@ -988,7 +998,7 @@ def run_ours(args):
     }
     # last key of the line: the compact record of every extra's figures
     line["summary"] = summary(extras, fp32_extra, line["extras"][f"solve_{other}"] if other == "df32" else {},
-                              cpu, timeouts)
+                              cpu, timeouts, link, rates["fp64_fma_per_s"])
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

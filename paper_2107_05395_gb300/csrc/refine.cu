@@ -1142,12 +1142,15 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
       }
     }
     if (fused && foff < (size_t)kMaxDynSmem) {
-      // a 16-row ring with as many threads (256 to 512) as fit beside the
-      // coefficients, else an 8-row ring; else the passes below
+      // a 16-row ring when 512 threads fit with it beside the coefficients, else an
+      // 8-row ring with as many threads (256 to 512) as fit; else the passes below.
+      // (For the double-float residual, which is bound by instruction issue, 512
+      // threads with 8 rows beat 448 with 16: 16.0 against 17.5 ms on the 3-group
+      // workload.)
       const size_t room = (size_t)kMaxDynSmem - foff;
       auto fit = [&](int D) { return (int)std::min<size_t>(kStagedThreads, room / fused_ring_bytes<TB>(D, 1) / 32 * 32); };
       int D = 16, threads = fit(16);
-      if (threads < 256) {
+      if (threads < kStagedThreads) {
         D = 8;
         threads = fit(8);
       }
