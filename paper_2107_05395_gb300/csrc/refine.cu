@@ -731,25 +731,29 @@ constexpr size_t pair_ring_bytes(int D, int threads) {
 }
 
 // One step: ODD == false runs sweep 0 of tile A and sweep 2 of tile B (upwards),
-// ODD == true sweep 1 of A and sweep 3 of B (downwards).  Ring use per slot: even
-// steps b of A (f1), g and x of B (f2, rx) and B's b, P rows behind (f3); odd steps
-// g of A (f1), A's b, P rows behind (f2), g and x of B (f3, rx).
-template <int P, bool DFRES, int D, bool ODD>
+// ODD == true sweep 1 of A and sweep 3 of B (downwards); HA / HB: the warp has tile
+// A / B in this step.  Ring use per slot: even steps b of A (f1), g and x of B (f2,
+// rx) and B's b, P rows behind (f3); odd steps g of A (f1), A's b, P rows behind
+// (f2), g and x of B (f3, rx).  The batches between the first and the last take
+// every row without the range tests.
+template <int P, bool DFRES, int D, bool ODD, bool HA, bool HB>
 __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
                                           const typename Residual<DFRES>::AC* arow, int N, int64_t ld,
-                                          const TileRef& A, bool hasA, const TileRef& B, bool hasB, double* rx,
-                                          float* f1, float* f2, float* f3, int T) {
+                                          const TileRef& A, const TileRef& B, double* rx, float* f1, float* f2,
+                                          float* f3, int T) {
   using RS = Residual<DFRES>;
   using X = typename RS::X;
   using F = NativeArith<float>;
   constexpr int W = P + 1;
   constexpr int NB = 2 * P + 1;
   constexpr int K = kStageBatch;
+  static_assert(K >= P, "the first batch covers the P rows of lag");
+  constexpr bool RES = ODD ? HA : HB;  // the tile in a merged sweep
   const float* lu_f = cf;
   const float* lu_b = cf + W * N;
   const float* ul_f = cr;
   const float* ul_b = cr + W * N;
-  const bool a = hasA && A.ok, b = hasB && B.ok;  // this lane copies and stores
+  const bool a = HA && A.ok, b = HB && B.ok;  // this lane copies and stores
   auto row = [&](int s) { return ODD ? N - 1 - s : s; };
   auto issue = [&](int s) {
     const int sl = (s & (D - 1)) * T;
@@ -769,7 +773,7 @@ __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
         }
       }
     }
-    if (s >= P && s < N + P) {
+    if (RES && s >= P && s < N + P) {
       const int64_t j = row(s - P);
       if (!ODD && b) cp_async<4>(f3 + sl, B.b + j * ld);
       if (ODD && a) cp_async<4>(f2 + sl, A.b + j * ld);
@@ -795,8 +799,9 @@ __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
   for (int s = 0; s < D; ++s) issue(s);
   float ua1 = 0.f, ua2 = 0.f, da1 = 0.f, da2 = 0.f;  // tile A: forward, backward recurrences
   float ub1 = 0.f, ub2 = 0.f, db1 = 0.f, db2 = 0.f;  // tile B
-  const bool res = ODD ? hasA : hasB;                 // the tile in a merged sweep
-  for (int s0 = 0; s0 < N + P; s0 += K) {
+  // rows s0 .. s0+K-1; GUARD: test them against 0 .. N-1 and the lag
+  auto batch = [&](int s0, auto guard) {
+    constexpr bool GUARD = decltype(guard)::value;
     cp_wait<D - K>();  // the groups of iterations s0 .. s0+K-1 are complete
     float r[K];
 #pragma unroll
@@ -804,16 +809,16 @@ __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
       const int s = s0 + q;
       const int sl = (s & (D - 1)) * T;
       double xi = 0.0;
-      if (s < N) {
+      if (!GUARD || s < N) {
         const int64_t i = row(s);
-        if (!ODD) {
-          if (hasA) {  // A, sweep 0: forward from the top
+        if constexpr (!ODD) {
+          if constexpr (HA) {  // A, sweep 0: forward from the top
             const float u = F::step<P, false>(lu_f + W * i, f1[sl], ua1, ua2);
             ua2 = ua1;
             ua1 = u;
             if (a) A.g[i * ld] = u;
           }
-          if (hasB) {  // B, sweep 2: backward of pass 1 (bottom elimination), x_1 = x_0 + d
+          if constexpr (HB) {  // B, sweep 2: backward of pass 1 (bottom elimination), x_1 = x_0 + d
             const float d = F::step<P, true>(ul_b + W * i, f2[sl], db1, db2);
             db2 = db1;
             db1 = d;
@@ -821,13 +826,13 @@ __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
             if (b) st_stream(B.x + i * ld, xi);
           }
         } else {
-          if (hasB) {  // B, sweep 3: backward of pass 2, x_2 = x_1 + d
+          if constexpr (HB) {  // B, sweep 3: backward of pass 2, x_2 = x_1 + d
             const float d = F::step<P, true>(lu_b + W * i, f3[sl], db1, db2);
             db2 = db1;
             db1 = d;
             if (b) st_stream(B.x + i * ld, rx[sl] + widen_f32(d));
           }
-          if (hasA) {  // A, sweep 1: backward of pass 0, x_0 = d
+          if constexpr (HA) {  // A, sweep 1: backward of pass 0, x_0 = d
             const float d = F::step<P, true>(lu_b + W * i, f1[sl], da1, da2);
             da2 = da1;
             da1 = d;
@@ -836,32 +841,41 @@ __device__ __forceinline__ void pair_step(const float* cf, const float* cr,
           }
         }
       }
-      push(xi);
-      r[q] = (res && s >= P && s < N + P)
-                 ? RS::template eval<NB>(arow + NB * row(s - P), xw, ODD ? f2[sl] : f3[sl])
-                 : 0.f;
+      if constexpr (RES) {
+        push(xi);
+        r[q] = (!GUARD || (s >= P && s < N + P))
+                   ? RS::template eval<NB>(arow + NB * row(s - P), xw, ODD ? f2[sl] : f3[sl])
+                   : 0.f;
+      }
     }
+    if constexpr (RES) {
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const int s = s0 + q;
-      if (res && s >= P && s < N + P) {
-        const int64_t j = row(s - P);
-        if (!ODD) {  // B: pass 2's forward step (top elimination)
-          const float u = F::step<P, false>(lu_f + W * j, r[q], ub1, ub2);
-          ub2 = ub1;
-          ub1 = u;
-          if (b) B.g[j * ld] = u;
-        } else {  // A: pass 1's forward step (bottom elimination)
-          const float u = F::step<P, false>(ul_f + W * j, r[q], ua1, ua2);
-          ua2 = ua1;
-          ua1 = u;
-          if (a) A.g[j * ld] = u;
+      for (int q = 0; q < K; ++q) {
+        const int s = s0 + q;
+        if (!GUARD || (s >= P && s < N + P)) {
+          const int64_t j = row(s - P);
+          if constexpr (!ODD) {  // B: pass 2's forward step (top elimination)
+            const float u = F::step<P, false>(lu_f + W * j, r[q], ub1, ub2);
+            ub2 = ub1;
+            ub1 = u;
+            if (b) B.g[j * ld] = u;
+          } else {  // A: pass 1's forward step (bottom elimination)
+            const float u = F::step<P, false>(ul_f + W * j, r[q], ua1, ua2);
+            ua2 = ua1;
+            ua1 = u;
+            if (a) A.g[j * ld] = u;
+          }
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) issue(s0 + D + q);  // refills the K slots used above
-  }
+  };
+  const int last = RES ? N + P : N;  // iterations of this step
+  batch(0, std::true_type{});
+  int s0 = K;
+  for (; s0 + K <= N; s0 += K) batch(s0, std::false_type{});
+  for (; s0 < last; s0 += K) batch(s0, std::true_type{});
   cp_wait<0>();
   __threadfence_block();  // the stores of g and x before the copies of the next step
 }
@@ -903,10 +917,21 @@ grouped_refined_pair_kernel(const __grid_constant__ Groups<float, float, double>
     const int64_t ka = s >> 1, kb = ka - 1;  // tile in sweep s % 2, tile in sweep s % 2 + 2
     const bool hasA = ka < nt, hasB = kb >= 0;
     const TileRef A = ref(hasA ? ka : 0), B = ref(hasB ? kb : 0);
-    if (s & 1)
-      pair_step<P, DFRES, D, true>(cs, crs, as, N, ld, A, hasA, B, hasB, rx, f1, f2, f3, T);
-    else
-      pair_step<P, DFRES, D, false>(cs, crs, as, N, ld, A, hasA, B, hasB, rx, f1, f2, f3, T);
+    if (s & 1) {
+      if (hasA && hasB)
+        pair_step<P, DFRES, D, true, true, true>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+      else if (hasA)
+        pair_step<P, DFRES, D, true, true, false>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+      else
+        pair_step<P, DFRES, D, true, false, true>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+    } else {
+      if (hasA && hasB)
+        pair_step<P, DFRES, D, false, true, true>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+      else if (hasA)
+        pair_step<P, DFRES, D, false, true, false>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+      else
+        pair_step<P, DFRES, D, false, false, true>(cs, crs, as, N, ld, A, B, rx, f1, f2, f3, T);
+    }
   }
 }
 
