@@ -536,7 +536,9 @@ __device__ __forceinline__ void fused_merged_pass(const float* bw, const float* 
 #pragma unroll
   for (int s = 0; s < D; ++s) issue(s);
   float d1 = 0.f, d2 = 0.f, u1 = 0.f, u2 = 0.f;
-  for (int s0 = 0; s0 < N + P; s0 += K) {
+  // rows s0 .. s0+K-1; GUARD: test them against 0 .. N-1 and the lag
+  auto batch = [&](int s0, auto guard) {
+    constexpr bool GUARD = decltype(guard)::value;
     cp_wait<D - K>();  // the groups of iterations s0 .. s0+K-1 are complete
     float r[K];
 #pragma unroll
@@ -544,7 +546,7 @@ __device__ __forceinline__ void fused_merged_pass(const float* bw, const float* 
       const int s = s0 + q;
       const int sl = (s & (D - 1)) * T;
       double xi = 0.0;
-      if (s < N) {
+      if (!GUARD || s < N) {
         const int i = row(s);
         const float d = F::step<P, true>(bw + W * i, rg[sl], d1, d2);
         d2 = d1;
@@ -553,12 +555,12 @@ __device__ __forceinline__ void fused_merged_pass(const float* bw, const float* 
         st_stream(xp + (int64_t)i * ld, xi);
       }
       push(xi);
-      r[q] = (s >= P && s < N + P) ? RS::template eval<NB>(arow + NB * row(s - P), xw, rb[sl]) : 0.f;
+      r[q] = (!GUARD || (s >= P && s < N + P)) ? RS::template eval<NB>(arow + NB * row(s - P), xw, rb[sl]) : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int s = s0 + q;
-      if (s >= P && s < N + P) {
+      if (!GUARD || (s >= P && s < N + P)) {
         const int j = row(s - P);
         const float u = F::step<P, false>(fw + W * j, r[q], u1, u2);
         gp[(int64_t)j * ld] = u;
@@ -568,7 +570,12 @@ __device__ __forceinline__ void fused_merged_pass(const float* bw, const float* 
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) issue(s0 + D + q);  // refills the K slots used above
-  }
+  };
+  static_assert(K >= P, "the first batch covers the P rows of lag");
+  batch(0, std::true_type{});
+  int s0 = K;
+  for (; s0 + K <= N; s0 += K) batch(s0, std::false_type{});
+  for (; s0 < N + P; s0 += K) batch(s0, std::true_type{});
   cp_wait<0>();
   __threadfence_block();  // the stores of g and x before the copies of the next pass
 }
@@ -593,12 +600,13 @@ __device__ __forceinline__ void fused_last_pass(const float* bw, int N, int64_t 
 #pragma unroll
   for (int s = 0; s < D; ++s) issue(s);
   float d1 = 0.f, d2 = 0.f;
-  for (int s0 = 0; s0 < N; s0 += K) {
+  auto batch = [&](int s0, auto guard) {
+    constexpr bool GUARD = decltype(guard)::value;
     cp_wait<D - K>();
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int s = s0 + q;
-      if (s < N) {
+      if (!GUARD || s < N) {
         const int sl = (s & (D - 1)) * T;
         const int i = row(s);
         const float d = F::step<P, true>(bw + W * i, rg[sl], d1, d2);
@@ -609,7 +617,10 @@ __device__ __forceinline__ void fused_last_pass(const float* bw, int N, int64_t 
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) issue(s0 + D + q);
-  }
+  };
+  int s0 = 0;
+  for (; s0 + K <= N; s0 += K) batch(s0, std::false_type{});
+  for (; s0 < N; s0 += K) batch(s0, std::true_type{});
   cp_wait<0>();
 }
 
