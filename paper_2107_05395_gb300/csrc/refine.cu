@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "sb_internal.h"
+#include "narrow.cuh"
 #include "sweep_tile.cuh"
 
 namespace sb {

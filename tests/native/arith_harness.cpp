@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "../../paper_2107_05395_gb300/csrc/arith.cuh"
+#include "../../paper_2107_05395_gb300/csrc/narrow.cuh"
 
 using namespace sb;
 

@@ -1,6 +1,7 @@
-"""CPU tests of the double-float arithmetic used by the SB_ARITH_DF32 sweeps.
+"""CPU tests of the double-float arithmetic used by the SB_ARITH_DF32 sweeps and of
+the integer FP64 -> FP32 truncation of the refinement residuals.
 
-The library's own header (paper_2107_05395_gb300/csrc/arith.cuh) is compiled for
+The library's own headers (paper_2107_05395_gb300/csrc/arith.cuh, narrow.cuh) are compiled for
 the host (tests/native/arith_harness.cpp, -ffp-contract=off) and checked against
 exact rational arithmetic: the FP64 -> pair split, the pair -> FP64 rounding, the
 sweep step, and whole sweeps against the FP64 oracle."""
