@@ -284,7 +284,7 @@ int sb_autotune(const sb_factor* f, int transpose, const void* rhs, sb_dtype rhs
                 sb_shape* best, float* best_ms);
 
 /*
- * Shared matrices of the finite-difference workloads (S1 of the hot path).
+ * Shared matrices of the finite-difference workloads (sections 3.2, 4.2 and 5.1).
  * Each is I + coef * K for an operator K:
  *   SB_MAT_DIFFUSION_DIRICHLET  K = tridiag(-1, 2, -1) with the stencil truncated at
  *                               the first and last rows (backward-Euler / left-hand
@@ -339,10 +339,11 @@ int sb_solve_batched_host(const sb_factor* f, int transpose, const void* rhs_hos
                           size_t work_bytes, void* stream);
 
 /*
- * Mixed precision with iterative refinement (S7 of the hot path): FP32 storage of
- * the right-hand sides, FP32 sweeps with the FP64 factors rounded to FP32, and
- * n_refine correction passes  r = b - A x,  d = A_32^{-1} r,  x += d  whose
- * residual uses A's FP64 entries, evaluated in FP64 (residual_arith =
+ * Mixed precision with iterative refinement (no counterpart in the paper, which
+ * does not discuss precision; the sweeps are those of sections 3.1 and 4.1): FP32
+ * storage of the right-hand sides, FP32 sweeps with the FP64 factors rounded to
+ * FP32, and n_refine correction passes  r = b - A x,  d = A_32^{-1} r,  x += d
+ * whose residual uses A's FP64 entries, evaluated in FP64 (residual_arith =
  * SB_ARITH_NATIVE) or double-float (SB_ARITH_DF32).  The solution is FP64.
  *
  *   rhs        device FP32, N x ld interleaved;  x  device FP64, same layout
@@ -351,8 +352,13 @@ int sb_solve_batched_host(const sb_factor* f, int transpose, const void* rhs_hos
  *   work       device workspace of sb_refine_workspace_bytes() bytes (FP32, one
  *              element per solution element), owned by the caller; unused when
  *              n_refine == 0 (may be NULL then).  Its contents are scratch.
- * Each pass is one kernel: the residual is built from a window of x inside the
- * forward sweep, so a pass reads b and x and writes x once (plus the workspace).
+ * One kernel runs every pass of a tile of 32 systems before its next tile.  The
+ * residual of a pass is built from a window of x inside the backward sweep of the
+ * pass before it, with the passes eliminating alternately from the top (A = LU)
+ * and from the bottom (the factors of the row- and column-reversed matrix, made
+ * once at factor time); where those factors or the shared memory they need are
+ * missing, each pass runs its own forward and backward sweeps in the same kernel.
+ * The result does not depend on the launch shape beyond rounding.
  */
 int sb_refine_workspace_bytes(const sb_factor* f, int64_t M, int64_t ld, size_t* bytes);
 int sb_solve_batched_refined(const sb_factor* f, const float* rhs, double* x, int64_t M,
@@ -395,7 +401,7 @@ int sb_solve_batched_refined_noalloc(const sb_factor* f, const float* rhs, doubl
  *                                        the residual), x_dtype SB_F64 and arith
  *                                        SB_ARITH_NATIVE (FP32 sweeps).
  *   residual_arith                       as for sb_solve_batched_refined.
- * Passes: 1 + n_refine launches in total, whatever G is.
+ * Launches: one per call, whatever G and n_refine are.
  */
 int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const* rhs,
                             void* const* x, const int64_t* M, const int64_t* ld,
@@ -404,7 +410,8 @@ int sb_solve_batched_groups(int G, const sb_factor* const* f, const void* const*
                             void* stream);
 
 /*
- * Implicit time steppers with a shared matrix (S4 + S10 of the hot path).
+ * Implicit time steppers with a shared matrix (sections 3.2, 4.2 and 5.1), each
+ * step one fused kernel, runs of steps replayed as CUDA graphs.
  * One step solves  A C^{n+1} = B C^n + E (C^3 - C)^n  for every simulation:
  *   SB_STEP_DIFFUSION      A = I + coef K, K = tridiag(-1, 2, -1) with Dirichlet rows.
  *                          SB_SCHEME_BE: B = I (backward Euler, coef = r = dt/dx^2);
@@ -524,7 +531,7 @@ int sb_stepper_run_coarsening(sb_stepper* st, double* state, int64_t M, int64_t 
                               void* stream);
 
 /*
- * Differentiable rollouts (S8 + S9 of the hot path; no counterpart in the paper,
+ * Differentiable rollouts (no counterpart in the paper,
  * which only runs forward).  For a backward-Euler diffusion / hyperdiffusion or a
  * Cahn-Hilliard stepper, the rollout x_{n+1} = A(p)^{-1} F(x_n), n < nsteps, with p
  * the stepper's coefficient (r, or gamma), and a loss L(x_T) chosen by the caller:
