@@ -1011,11 +1011,16 @@ __device__ __forceinline__ void rhs_tile(const double* rc, int N, int64_t M, int
 // STAGED: the FP32 pass and the correction passes stream their rows through the
 // shared-memory ring at ring_off (512 threads, one CTA per SM), as in the grouped
 // refined solve.
-template <int P, bool DFRES, int NB, bool HAS_E, bool STAGED>
-__global__ void __launch_bounds__(STAGED ? kStagedThreads : 256, STAGED ? 1 : 2)
+// FORM 0: register-prefetched passes (256 threads, two CTAs per SM); 1: passes
+// staged through the shared-memory ring; 2: the merged passes of
+// refine_fused_tile with a ring of D rows (the rows of J A J staged after the
+// FP32 sweep rows).
+template <int P, bool DFRES, int NB, bool HAS_E, int FORM, int D = 16>
+__global__ void __launch_bounds__(FORM > 0 ? kStagedThreads : 256, FORM > 0 ? 1 : 2)
 refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, double* f,
                     const double* __restrict__ rcoef, int n_refine, unsigned ring_off) {
   using AC = typename Residual<DFRES>::AC;
+  constexpr bool STAGED = FORM == 1;
   constexpr int W = P + 1;
   constexpr int NBA = 2 * P + 1;
   constexpr int RW = NB + (HAS_E ? 3 : 0);
@@ -1023,16 +1028,21 @@ refined_step_kernel(const __grid_constant__ Groups<float, double, double> a, dou
   const int N = a.N[0];
   AC* as = reinterpret_cast<AC*>(smem_raw);          // A rows (8-byte values)
   float* cs = reinterpret_cast<float*>(as + NBA * N);  // FP32 sweep rows
-  double* rs = reinterpret_cast<double*>(cs + 2 * W * N);  // right-hand-side rows (8-byte aligned)
+  float* crs = cs + 2 * W * N;                         // the same of J A J (FORM 2)
+  double* rs = reinterpret_cast<double*>(cs + (FORM == 2 ? 4 : 2) * W * N);  // right-hand-side rows (8-byte aligned)
   stage(as, static_cast<const AC*>(a.arow[0]), NBA * N);
   stage(cs, a.coef[0], 2 * W * N);
+  if constexpr (FORM == 2) stage(crs, a.rcoef[0], 2 * W * N);
   stage(rs, rcoef, RW * N);
   __syncthreads();
   const int nw = blockDim.x >> 5;
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); tile < a.ntiles[0];
        tile += (int64_t)gridDim.x * nw) {
     rhs_tile<NB, HAS_E, kFusedRows>(rs, N, a.M[0], a.ld[0], a.x[0], f, tile);
-    if constexpr (STAGED) {
+    if constexpr (FORM == 2) {
+      refine_fused_tile<P, DFRES, double, D>(cs, crs, as, N, a.M[0], a.ld[0], f, a.x[0], a.work[0], tile,
+                                             smem_raw + ring_off, n_refine);
+    } else if constexpr (STAGED) {
       sweep32_tile_staged<P, double>(cs, cs + W * N, N, a.M[0], a.ld[0], f, a.x[0], a.work[0], tile,
                                      smem_raw + ring_off);
       for (int k = 0; k < n_refine; ++k)
@@ -1235,11 +1245,29 @@ int launch_refined_step(const sb_factor* f, const double* rcoef, double* state, 
                       (size_t)RW * f->N * sizeof(double);
   if (smem > 227 * 1024) return fail(SB_ERR_UNSUPPORTED, "N=%lld: the step's coefficients exceed shared memory",
                                      (long long)f->N);
+  // with the FP64 residual, the merged passes when the rows of J A J exist and,
+  // with them, a 16-row ring for 512 threads fits beside the coefficients (CH
+  // N = 256, 2^20 systems, two passes: 10.3 -> 9.9 ms; with the double-float
+  // residual they were slower, 8.2 -> 8.5 ms, and are not used)
+  a.rcoef[0] = f->coef32_rev;
+  const size_t foff = (smem + (size_t)2 * (P + 1) * f->N * sizeof(float) + 15) / 16 * 16;
+  if (!DFRES && n_refine > 0 && f->coef32_rev &&
+      foff + fused_ring_bytes<double>(16, kStagedThreads) <= (size_t)kMaxDynSmem) {
+    auto k = refined_step_kernel<P, false, NB, HAS_E, 2, 16>;
+    const size_t smem_all = foff + fused_ring_bytes<double>(16, kStagedThreads);
+    int total = 0;
+    SB_TRY(resident_ctas(k, f->device, smem_all, &total, kStagedThreads));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ntiles[0], total));
+    a.cta_begin[0] = 0;
+    a.cta_begin[1] = (int)grid;
+    k<<<(unsigned)grid, kStagedThreads, smem_all, stream>>>(a, fbuf, rcoef, n_refine, (unsigned)foff);
+    return cuda_check(cudaGetLastError(), "refined step launch");
+  }
   // the staged passes when their ring fits beside the coefficients
   const size_t ring_off = (smem + 15) / 16 * 16;
   const bool staged = kRefinedStepStaged && n_refine > 0 &&
                       ring_off + stage_ring_bytes<double>(kStagedThreads) <= (size_t)kMaxDynSmem;
-  auto k = staged ? refined_step_kernel<P, DFRES, NB, HAS_E, true> : refined_step_kernel<P, DFRES, NB, HAS_E, false>;
+  auto k = staged ? refined_step_kernel<P, DFRES, NB, HAS_E, 1> : refined_step_kernel<P, DFRES, NB, HAS_E, 0>;
   const int threads = staged ? kStagedThreads : kThreads;
   const size_t smem_all = staged ? ring_off + stage_ring_bytes<double>(kStagedThreads) : smem;
   int total = 0;
