@@ -399,7 +399,8 @@ def sb_solve_batched_refined_noalloc(f: Factor, rhs, x, n_refine=2, residual_ari
 
 def sb_solve_batched_groups(factors, rhs, x, arith="native", n_refine=0, residual_arith="native",
                             work=None, Ms=None, lds=None, stream=None):
-    """One launch per pass over several shared-LHS groups (lists of equal length)."""
+    """One launch over several shared-LHS groups (lists of equal length), every
+    pass of a refined solve included."""
     G = len(factors)
     shapes = [_batch_shape(rhs[g], factors[g].N, None if Ms is None else Ms[g],
                            None if lds is None else lds[g]) for g in range(G)]

@@ -147,6 +147,31 @@ def test_groups_without_refinement(env, arith, rt, xt, tol):
         assert np.max(relerr_per_system(to_host(xs[g]), refs[g])) <= tol, g
 
 
+@pytest.mark.parametrize("kind", ["tri", "penta"])
+@pytest.mark.parametrize("n_refine,residual", [(1, "native"), (2, "native"), (2, "df32"), (3, "native")])
+def test_refined_groups_of_different_n(env, kind, n_refine, residual):
+    """Refined solves of three groups of different N in one launch, in every pass
+    form the launch can pick: two FP64-residual passes take the paired tiles, the
+    other counts and the double-float residual the single-tile merged passes.
+    Every system of every group is checked against the oracle."""
+    sb, torch = env
+    Ns, Ms = (5, 64, 300), (1000, 77, 3001)
+    facs, refs, rhs, xs, work = [], [], [], [], []
+    for g, (N, M) in enumerate(zip(Ns, Ms)):
+        fac, ref_fn = make(sb, kind, N, seed=200 + g)
+        h = synth.rhs_uniform(seed=g + 7, N=N, M=M, ld=M, dtype=np.float32, pad_value=0.0)
+        facs.append(fac)
+        refs.append(ref_fn(h.astype(np.float64)))
+        rhs.append(to_dev(h, torch))
+        xs.append(torch.zeros((N, M), dtype=torch.float64, device="cuda"))
+        work.append(torch.empty((N, M), dtype=torch.float32, device="cuda"))
+    sb.sb_solve_batched_groups(facs, rhs, xs, n_refine=n_refine, residual_arith=residual, work=work)
+    torch.cuda.synchronize()
+    for g in range(3):
+        err = np.max(relerr_per_system(to_host(xs[g]), refs[g]))
+        assert err <= (1e-10 if n_refine >= 2 else 1e-9), (g, err)
+
+
 def test_groups_reject_mixed_bandwidth(env):
     sb, torch = env
     f1, _ = make(sb, "tri", 8, 1)
