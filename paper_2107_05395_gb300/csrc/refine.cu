@@ -1165,22 +1165,18 @@ int launch_grouped_refined_solve(const std::vector<const sb_factor*>& f, const s
                                   (size_t)4 * (P + 1) * f[g]->N * sizeof(float));
     }
     const size_t foff = (fsmem + 15) / 16 * 16;
-    // two refinements with the FP64 residual: tiles paired two sweeps apart, with a
-    // 16-row ring when 384 or more threads fit beside the coefficients, else an
-    // 8-row ring.  (The double-float residual leaves the FP64 pipe idle anyway and
-    // is bound by instruction issue, which the paired loops raise: it takes the
+    // two refinements with the FP64 residual: tiles paired two sweeps apart, with an
+    // 8-row ring and as many threads (256 to 512) as fit beside the coefficients.
+    // (A 16-row ring spills registers: 21.0 against 16.3 ms on the 3-group
+    // workload.  The double-float residual leaves the FP64 pipe idle anyway and is
+    // bound by instruction issue, which the paired loops raise: it takes the
     // single-tile form below.)
     if (!DFRES && fused && n_refine == 2 && foff < (size_t)kMaxDynSmem) {
       const size_t room = (size_t)kMaxDynSmem - foff;
-      auto fit = [&](int D) { return (int)std::min<size_t>(kStagedThreads, room / pair_ring_bytes(D, 1) / 32 * 32); };
-      int D = 16, threads = fit(16);
-      if (threads < 384) {
-        D = 8;
-        threads = fit(8);
-      }
+      const int threads = (int)std::min<size_t>(kStagedThreads, room / pair_ring_bytes(8, 1) / 32 * 32);
       if (threads >= 256) {
-        const size_t total_smem = foff + pair_ring_bytes(D, threads);
-        auto k = D == 16 ? grouped_refined_pair_kernel<P, false, 16> : grouped_refined_pair_kernel<P, false, 8>;
+        const size_t total_smem = foff + pair_ring_bytes(8, threads);
+        auto k = grouped_refined_pair_kernel<P, false, 8>;
         int total = 0;
         SB_TRY(resident_ctas(k, f[0]->device, total_smem, &total, threads));
         const int grid = plan(a, f, total);

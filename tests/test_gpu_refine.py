@@ -64,10 +64,10 @@ def test_refinement_passes_alternate_direction(env, kind, N, M, residual):
     (A = LU) for even k and from the bottom (the rows of J A J) for odd k, each
     correction pass merged into the backward sweep before it.  One to four passes
     cover both directions of the merged and of the last pass (n = 2 with the FP64
-    residual runs the paired-tile form).  Shared memory holds the coefficients and a
-    ring per thread: 16 rows (512 threads) for N <= 37, 8 rows for tri N = 2048 and
-    penta N = 1400 (512 threads) and penta N = 2000 (416 threads); penta N = 2400
-    leaves no room and runs the separate passes.
+    residual runs the paired-tile form, always with an 8-row ring).  Shared memory
+    holds the coefficients and a ring per thread: 16 rows (512 threads) for N <= 37,
+    8 rows for tri N = 2048 and penta N = 1400 (512 threads) and penta N = 2000
+    (416 threads); penta N = 2400 leaves no room and runs the separate passes.
     The random matrices are nonsymmetric, so a wrong reversal of J A J's diagonals
     stops the contraction."""
     sb, torch = env
