@@ -246,30 +246,16 @@ static int upload_factor(sb_factor* f) {
   SB_CUDA(cudaMemcpy(f->arow64, arow.data(), arow.size() * sizeof(double), cudaMemcpyHostToDevice));
   SB_CUDA(cudaMemcpy(f->arowdf, arowdf.data(), arowdf.size() * sizeof(float), cudaMemcpyHostToDevice));
   // FP32 sweep rows of J A J (the rows and columns of A in reverse order) for the
-  // refinement passes that eliminate from the bottom: the diagonal at offset o of
-  // J A J is A's diagonal at offset -o, read backwards.  Its rows are stored at the
-  // index of the row of A they act on.  A zero pivot of J A J only disables them.
+  // refinement passes that eliminate from the bottom, stored at the index of the
+  // row of A they act on (two_ended.h).  A zero pivot of J A J only disables them.
   if (!f->periodic) {
-    const int P = f->P;
-    std::vector<std::vector<double>> rd(nb, std::vector<double>(N, 0.0));
-    for (int64_t k = 0; k < nb; ++k)
-      for (int64_t i = 0; i < N; ++i) rd[k][i] = f->h_diag[(size_t)(2 * P - k) * N + (N - 1 - i)];
-    std::vector<double> rc;
-    const int rrc = P == 1 ? factor_tri_host(N, rd[0].data(), rd[1].data(), rd[2].data(), rc)
-                           : factor_penta_host(N, rd[0].data(), rd[1].data(), rd[2].data(), rd[3].data(),
-                                               rd[4].data(), rc);
-    if (rrc == SB_OK) {
-      const int64_t W = P + 1;
-      std::vector<float> rev((size_t)2 * W * N);
-      for (int64_t i = 0; i < N; ++i)
-        for (int64_t c = 0; c < W; ++c) {
-          rev[(size_t)(W * i + c)] = (float)rc[(size_t)(W * (N - 1 - i) + c)];                  // forward
-          rev[(size_t)(W * N + W * i + c)] = (float)rc[(size_t)(W * N + W * (N - 1 - i) + c)];  // backward
-        }
+    std::vector<double> rfw, rbw;
+    if (reversed_rows(f->P, (int)N, f->h_diag.data(), rfw, rbw)) {
+      std::vector<float> rev(rfw.size() + rbw.size());
+      for (size_t k = 0; k < rfw.size(); ++k) rev[k] = (float)rfw[k];
+      for (size_t k = 0; k < rbw.size(); ++k) rev[rfw.size() + k] = (float)rbw[k];
       SB_CUDA(cudaMalloc(&f->coef32_rev, rev.size() * sizeof(float)));
       SB_CUDA(cudaMemcpy(f->coef32_rev, rev.data(), rev.size() * sizeof(float), cudaMemcpyHostToDevice));
-    } else {
-      clear_error();
     }
   }
   // images of the partitioned solve of A and A^T (FP32) for each variant: chunks of

@@ -74,6 +74,30 @@ bool two_ended_eliminate(int P, int N, int n, Diag d, double* fw, double* bw) {
   return true;
 }
 
+// Sweep rows of the whole reversed matrix J A J (the bottom half of the two-ended
+// form, extended to every row), stored at the index of the row of A they act on.
+// With them A x = b is solved from the other end: the forward sweep runs from row
+// N-1 down, u_i = F0_i b_i - F1_i u_{i+1} - F2_i u_{i+2}, and the backward sweep
+// from row 0 up, x_i = u_i - B1_i x_{i-1} - B2_i x_{i-2}.  Refinement passes that
+// alternate their direction use them.  diag as for build_two_ended.  False on a
+// zero or non-finite pivot of J A J.
+inline bool reversed_rows(int P, int N, const double* diag, std::vector<double>& fw,
+                          std::vector<double>& bw) {
+  const int W = P + 1;
+  // reversed matrix: R[i][i+o] = A[N-1-i][N-1-i-o]
+  auto rev = [&](int o, int i) { return diag[(size_t)(P - o) * N + (N - 1 - i)]; };
+  std::vector<double> rf((size_t)W * N), rb((size_t)W * N);
+  if (!two_ended_eliminate(P, N, N, rev, rf.data(), rb.data())) return false;
+  fw.assign((size_t)W * N, 0.0);
+  bw.assign((size_t)W * N, 0.0);
+  for (int j = 0; j < N; ++j)  // reversed row j is row N-1-j of A
+    for (int k = 0; k < W; ++k) {
+      fw[(size_t)W * (N - 1 - j) + k] = rf[(size_t)W * j + k];
+      bw[(size_t)W * (N - 1 - j) + k] = rb[(size_t)W * j + k];
+    }
+  return true;
+}
+
 // Inverse of the n x n row-major matrix m (Gauss-Jordan with partial pivoting, FP64).
 // False if a pivot is zero or the result is not finite.
 inline bool two_ended_invert(int n, std::vector<double> m, std::vector<double>& inv) {

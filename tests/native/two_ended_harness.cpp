@@ -36,6 +36,36 @@ int h_two_ended_solve(int P, int N, const double* diag, int transpose, long M, c
   return t.s;
 }
 
+// Solves A x_m = b_m from the other end with the rows of J A J (reversed_rows):
+// forward sweep from row N-1 down, backward sweep from row 0 up.  Layout as for
+// h_two_ended_solve.  Returns 0, or -1 when J A J has a zero pivot.  rows (may be
+// NULL) receives [forward rows | backward rows], (P+1) values per row.
+int h_reversed_solve(int P, int N, const double* diag, long M, const double* b, double* x, double* rows) {
+  std::vector<double> fw, bw;
+  if (!reversed_rows(P, N, diag, fw, bw)) return -1;
+  const int W = P + 1;
+  if (rows) {
+    for (size_t k = 0; k < fw.size(); ++k) rows[k] = fw[k];
+    for (size_t k = 0; k < bw.size(); ++k) rows[fw.size() + k] = bw[k];
+  }
+  std::vector<double> u(N);
+  for (long m = 0; m < M; ++m) {
+    for (int i = N - 1; i >= 0; --i) {
+      double v = fw[(size_t)W * i] * b[(long)i * M + m];
+      if (i + 1 < N) v -= fw[(size_t)W * i + 1] * u[i + 1];
+      if (P == 2 && i + 2 < N) v -= fw[(size_t)W * i + 2] * u[i + 2];
+      u[i] = v;
+    }
+    for (int i = 0; i < N; ++i) {
+      double v = u[i];
+      if (i >= 1) v -= bw[(size_t)W * i + 1] * x[(long)(i - 1) * M + m];
+      if (P == 2 && i >= 2) v -= bw[(size_t)W * i + 2] * x[(long)(i - 2) * M + m];
+      x[(long)i * M + m] = v;
+    }
+  }
+  return 0;
+}
+
 // The device image [fw | bw | minv]; returns its length, or -1 when it cannot be
 // built or does not fit in cap.
 int h_two_ended_image(int P, int N, const double* diag, double* out, int cap) {
