@@ -725,8 +725,8 @@ grouped_refined_fused_kernel(const __grid_constant__ Groups<float, TB, double> a
 // (down, 1).  A warp whose tiles all sit in the same sweep leaves the FP64 pipe
 // idle in the first and the last one.  Here a warp carries two tiles two sweeps
 // apart, so every loop runs sweeps 0 and 2, or 1 and 3, of two different tiles
-// side by side: both in the same direction, with 4 FP64 operations and 36 bytes
-// per element pair in every loop.  Tile k of the warp runs its sweep p in step
+// side by side: both in the same direction, with 4 FP64 operations per element
+// pair in every loop (and 36 or 40 bytes).  Tile k of the warp runs its sweep p in step
 // 2k + p; steps 0, 1 and the last two carry a single tile.
 
 struct TileRef {
