@@ -11,6 +11,13 @@
 // launch runs every pass: each warp takes a tile through the FP32 pass and all
 // correction passes before its next tile.
 //
+// Forms, chosen by what fits in shared memory: (1) separate passes, their rows
+// staged through a shared-memory ring or prefetched into registers; (2) merged
+// passes, each correction pass run inside the backward sweep of the pass before it
+// (passes alternate between eliminating from the top and from the bottom, with
+// the rows of J A J); (3) for two passes with the FP64 residual, the merged passes
+// with two tiles per warp two sweeps apart, so that every loop has FP64 work.
+//
 // Groups: several shared-LHS factors (different N) are solved by one launch.  The
 // persistent CTAs are split between the groups in proportion to N*M; a CTA stages
 // its own group's coefficients once.
