@@ -24,3 +24,21 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_summary_keeps_every_extra_figure_compactly():
+    """The line's last key repeats the extras' figures; the refined multi-group
+    solve is set against its FP64-pipe bound (8 FP64 operations per element at the
+    FP64 FMA rate measured in the same run) and the host link rates are kept."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ex = {"multigroup_refine": {"elements": 1000000, "refine2_fp64_residual": {
+        "ms_per_call": 20.0, "launches": 1, "max_rel_err_per_group": [1e-16, 2e-16]}}}
+    s = bench.summary(ex, {}, {}, None, 0, {"h2d": 211.0, "d2h": 193.0, "both": 341.0}, 8e8)
+    assert s["multigroup_fp64_bound_ms"] == 10.0  # 1e6 x 8 / 8e8 s
+    assert s["multigroup_of_fp64_bound"] == 0.5
+    assert s["host_link_gbs"] == {"h2d": 211.0, "d2h": 193.0, "both": 341.0}
+    assert s["multigroup_launches"]["refine2_fp64_residual"] == 1
+    assert s["multigroup_max_err"] == 2e-16
+    empty = bench.summary({}, {}, {}, None, 0)
+    assert "multigroup_of_fp64_bound" not in empty and empty["host_link_gbs"] is None
